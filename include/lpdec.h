@@ -1,0 +1,181 @@
+/*
+ * liblpdec -- ADMM LP decoding of LDPC codes on a GB300 (sm_103a) GPU.
+ *
+ * The method is Algorithm 1 of "Decomposition Methods for Large Scale LP
+ * Decoding" (Barman, Liu, Draper, Recht), Section 3.3: the alternating
+ * direction method of multipliers applied to Feldman's LP relaxation
+ * (Section 2, eq. (feldmanLP)), with the check-side z-update computed by the
+ * two-slice projection onto the parity polytope (Section 4.4, Algorithm 2)
+ * and the over-relaxation of Section 5.2.
+ *
+ * Conventions for every entry point:
+ *   - Return value: LPDEC_OK (0) or a negative LPDEC_E* status.  A
+ *     human-readable message for the calling thread's last failure is
+ *     available from lpdec_last_error().
+ *   - "device pointer" means memory of the current CUDA device (cudaMalloc,
+ *     a torch CUDA tensor, ...).  "host pointer" means ordinary CPU memory.
+ *     The library never takes ownership of caller memory.
+ *   - Decode calls that take a stream are stream-ordered and asynchronous:
+ *     they return after enqueuing work on that stream; synchronize the stream
+ *     before reading outputs.  stream == NULL means the legacy default stream.
+ *   - All arithmetic on the GPU is FP32.  FP64 is used only to sum the
+ *     per-frame residual norms of the stopping test.
+ *   - Layouts are row-major: an LLR or x batch is [n_frames x n], frame f at
+ *     element offset f*n.
+ */
+#ifndef LPDEC_H
+#define LPDEC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LPDEC_API __attribute__((visibility("default")))
+#else
+#define LPDEC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define LPDEC_OK        0
+#define LPDEC_EINVAL   (-1) /* an argument is out of range or inconsistent */
+#define LPDEC_ENOMEM   (-2) /* a host or device allocation failed, or a size limit is exceeded */
+#define LPDEC_ECUDA    (-3) /* a CUDA runtime call failed (message has the CUDA error) */
+#define LPDEC_ETIMEOUT (-4) /* a wait ran out of time before the result was ready */
+#define LPDEC_EBUSY    (-5) /* a queue or budget is full; retry later */
+#define LPDEC_ECLOSED  (-6) /* the object was shut down */
+
+/* Per-frame iteration count written for a frame whose LLRs contain NaN/Inf:
+ * that frame is not decoded (x = 0, bits = 0, cert = 0). */
+#define LPDEC_FRAME_BAD_LLR (-1)
+
+/* ---- storage type of the per-edge z / lambda state --------------------- */
+#define LPDEC_STATE_F32  0
+#define LPDEC_STATE_BF16 1 /* round-to-nearest-even on every store; FP32 arithmetic */
+#define LPDEC_STATE_F16  2 /* round-to-nearest-even on every store; FP32 arithmetic */
+
+/* ---- schedules --------------------------------------------------------- */
+#define LPDEC_SCHED_AUTO     0 /* RESIDENT when a frame's state fits in shared memory, else STREAMED */
+#define LPDEC_SCHED_STREAMED 1 /* one kernel launch per ADMM iteration (or iters_per_launch); the
+                                  z/lambda state of every frame goes through device memory between
+                                  launches */
+#define LPDEC_SCHED_RESIDENT 2 /* one launch; each frame's z/lambda/x state stays in shared memory
+                                  for all of its iterations */
+
+typedef struct lpdec_code lpdec_code;     /* opaque: a parity-check matrix resident on one GPU */
+typedef struct lpdec_server lpdec_server; /* opaque: a continuous-batching decode server */
+
+/* Decoder parameters (Algorithm 1 caption; Section 5.1 for the paper's defaults). */
+typedef struct lpdec_params {
+    double  mu;               /* ADMM penalty mu > 0 (eq. (augLag)) */
+    double  rho;              /* over-relaxation rho in [1, 2) (Section 5.2) */
+    double  eps;              /* stopping tolerance eps >= 0: stop when
+                                 sum_j ||P_j x - z_j||^2 < eps^2 E and
+                                 sum_j ||z_j - z_j^old||^2 < eps^2 E (E = number of edges;
+                                 the paper's eps^2 M d for regular codes).
+                                 eps = 0: run exactly max_iter iterations. */
+    int32_t max_iter;         /* t_max >= 1 */
+    int32_t state_dtype;      /* LPDEC_STATE_* */
+    double  cert_tol;         /* certificate integrality tolerance, in (0, 0.5) */
+    int32_t schedule;         /* LPDEC_SCHED_* */
+    int32_t iters_per_launch; /* STREAMED only: ADMM iterations per kernel launch (>= 1) */
+    int32_t reserved[6];      /* must be zero */
+} lpdec_params;
+
+/* Fill *p with the paper's Section 5.1 settings: mu = 3, rho = 1.9, eps = 1e-5,
+ * max_iter = 1000, FP32 state, cert_tol = 1e-2, AUTO schedule, 1 iteration per launch. */
+LPDEC_API void lpdec_params_default(lpdec_params *p);
+
+/* Message describing the calling thread's most recent failure ("" if none). */
+LPDEC_API const char *lpdec_last_error(void);
+
+/* Library version string. */
+LPDEC_API const char *lpdec_version(void);
+
+/* ---- codes ------------------------------------------------------------- */
+
+/*
+ * Upload a parity-check matrix H (m x n) to the current CUDA device.
+ * Section 2 defines H, the neighbourhoods N_c(j), N_v(i) and the selection
+ * matrices P_j; the k-th edge of check j (in ascending column order) is the
+ * k-th row of P_j.
+ *   row_ptr[m+1], col_idx[E]: host pointers, H by rows (CSR); columns strictly
+ *                             ascending within a row.
+ *   col_ptr[n+1], row_idx[E]: host pointers, H by columns (CSC); rows strictly
+ *                             ascending within a column.
+ *   edge_perm[E]:             host pointer; edge_perm[t] is the CSR edge id of
+ *                             CSC slot t.
+ * The arrays are copied; the caller keeps ownership.
+ * Errors: LPDEC_EINVAL if n or m <= 0, any check degree is 0 or > 32, any
+ * variable degree is 0 (x_i is then undefined, Section 3.2), columns/rows are
+ * unsorted or repeated, or the three layouts disagree; LPDEC_ENOMEM / LPDEC_ECUDA
+ * on allocation or copy failure.  *out is set only on success.
+ */
+LPDEC_API int lpdec_code_create(int32_t n, int32_t m,
+                      const int32_t *row_ptr, const int32_t *col_idx,
+                      const int32_t *col_ptr, const int32_t *row_idx,
+                      const int32_t *edge_perm, lpdec_code **out);
+
+/* Shape of a code: n, m, number of edges E, largest check degree, and
+ * k_rank = n - rank_GF(2)(H).  Any output pointer may be NULL. */
+LPDEC_API int lpdec_code_info(const lpdec_code *code, int32_t *n, int32_t *m, int64_t *E,
+                    int32_t *max_dc, int32_t *k_rank);
+
+/* Free a code.  The caller must ensure no decode using it is still running. */
+LPDEC_API int lpdec_code_destroy(lpdec_code *code);
+
+/* ---- decoding ---------------------------------------------------------- */
+
+/*
+ * Decode a batch of frames of one code: Algorithm 1 per frame.
+ *   llr:       device pointer, [n_frames x n] FP32, gamma_i = log W(y_i|0)/W(y_i|1)
+ *              (Section 2; positive favours bit 0).
+ *   x_out:     device pointer, [n_frames x n] FP32: the x of the last iteration run.
+ *   bits_out:  device pointer, [n_frames x n] uint8: b_i = [x_i > 1/2] (Section 5.1 rounding).
+ *   iters_out: device pointer, [n_frames] int32: completed iterations when the stopping
+ *              test first passed, or max_iter; LPDEC_FRAME_BAD_LLR for a frame with a
+ *              non-finite LLR.
+ *   cert_out:  device pointer, [n_frames] uint8: 1 when the output is certified an ML
+ *              codeword (Section 1: an integral LP optimum is the ML codeword):
+ *              the residual test passes at the final iterate with tolerance
+ *              max(eps, 1e-5), every x_i is within cert_tol of 0 or 1, and b
+ *              satisfies every check.
+ * Any of bits_out, iters_out, cert_out may be NULL.  n_frames == 0 is a no-op.
+ * Errors (returned synchronously, before any work is queued): LPDEC_EINVAL for a
+ * NULL code/llr/x_out, n_frames < 0, mu <= 0, rho outside [1, 2), eps < 0,
+ * max_iter < 1, cert_tol outside (0, 0.5), an unknown state_dtype/schedule,
+ * iters_per_launch < 1, or a RESIDENT schedule whose frame state does not fit
+ * in shared memory; LPDEC_ENOMEM / LPDEC_ECUDA when workspace allocation or a
+ * launch fails.  The call allocates its device workspace stream-ordered
+ * (cudaMallocAsync) and frees it the same way.
+ */
+LPDEC_API int lpdec_decode(const lpdec_code *code, int32_t n_frames, const float *llr,
+                 const lpdec_params *params, float *x_out, uint8_t *bits_out,
+                 int32_t *iters_out, uint8_t *cert_out, void *cuda_stream);
+
+/*
+ * As lpdec_decode, but every buffer is a HOST pointer: the call copies llr to
+ * the device, decodes, copies the outputs back and synchronizes the stream
+ * before returning.  Outputs have the same meaning and shapes as above.
+ */
+LPDEC_API int lpdec_decode_host(const lpdec_code *code, int32_t n_frames, const float *llr,
+                      const lpdec_params *params, float *x_out, uint8_t *bits_out,
+                      int32_t *iters_out, uint8_t *cert_out, void *cuda_stream);
+
+/*
+ * Euclidean projection onto the parity polytope PP_d (Section 4.4, Algorithm 2)
+ * of `count` vectors of dimension d, 1 <= d <= 32, computed exactly as the
+ * decoder's check update computes it.
+ *   v: device pointer [count x d] FP32 inputs;  z: device pointer [count x d] outputs.
+ * Errors: LPDEC_EINVAL for d outside [1, 32], count < 0 or NULL pointers.
+ */
+LPDEC_API int lpdec_project(int32_t d, int64_t count, const float *v, float *z, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LPDEC_H */

@@ -1,0 +1,506 @@
+// C-ABI layer of liblpdec: argument validation, the code object, workspace,
+// tile selection and kernel launches.  Declarations and error semantics are
+// in include/lpdec.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "lpdec.h"
+#include "lpdec_api_internal.h"
+#include "lpdec_internal.h"
+
+using lpdec::DecodeArgs;
+
+// ---------------------------------------------------------------------------
+// errors
+namespace {
+thread_local std::string g_last_error;
+}
+
+namespace lpdec {
+int set_error(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+int cuda_error(cudaError_t e, const char *what) {
+    return set_error(e == cudaErrorMemoryAllocation ? LPDEC_ENOMEM : LPDEC_ECUDA, "%s: %s (%s)", what,
+                     cudaGetErrorString(e), cudaGetErrorName(e));
+}
+}  // namespace lpdec
+
+using lpdec::cuda_error;
+using lpdec::set_error;
+
+extern "C" const char *lpdec_last_error(void) { return g_last_error.c_str(); }
+extern "C" const char *lpdec_version(void) { return "liblpdec 0.1 (sm_103a)"; }
+
+extern "C" void lpdec_params_default(lpdec_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->mu = 3.0;
+    p->rho = 1.9;
+    p->eps = 1e-5;
+    p->max_iter = 1000;
+    p->state_dtype = LPDEC_STATE_F32;
+    p->cert_tol = 1e-2;
+    p->schedule = LPDEC_SCHED_AUTO;
+    p->iters_per_launch = 1;
+}
+
+// ---------------------------------------------------------------------------
+// code object
+
+// n - rank over GF(2) of H, by Gaussian elimination on packed rows.
+static int gf2_k_rank(int n, int m, const int32_t *row_ptr, const int32_t *col_idx) {
+    const int W = (n + 63) / 64;
+    std::vector<uint64_t> a((size_t)m * W, 0);
+    for (int j = 0; j < m; ++j)
+        for (int e = row_ptr[j]; e < row_ptr[j + 1]; ++e)
+            a[(size_t)j * W + col_idx[e] / 64] |= 1ull << (col_idx[e] % 64);
+    int rank = 0;
+    for (int col = 0; col < n && rank < m; ++col) {
+        const int wd = col / 64;
+        const uint64_t bit = 1ull << (col % 64);
+        int piv = -1;
+        for (int r = rank; r < m; ++r)
+            if (a[(size_t)r * W + wd] & bit) { piv = r; break; }
+        if (piv < 0) continue;
+        if (piv != rank)
+            for (int q = 0; q < W; ++q) std::swap(a[(size_t)piv * W + q], a[(size_t)rank * W + q]);
+        for (int r = 0; r < m; ++r)
+            if (r != rank && (a[(size_t)r * W + wd] & bit))
+                for (int q = wd; q < W; ++q) a[(size_t)r * W + q] ^= a[(size_t)rank * W + q];
+        ++rank;
+    }
+    return n - rank;
+}
+
+extern "C" int lpdec_code_create(int32_t n, int32_t m, const int32_t *row_ptr, const int32_t *col_idx,
+                                 const int32_t *col_ptr, const int32_t *row_idx, const int32_t *edge_perm,
+                                 lpdec_code **out) {
+    if (!out) return set_error(LPDEC_EINVAL, "lpdec_code_create: out is NULL");
+    if (n <= 0 || m <= 0) return set_error(LPDEC_EINVAL, "lpdec_code_create: n=%d m=%d must be positive", n, m);
+    if (!row_ptr || !col_idx || !col_ptr || !row_idx || !edge_perm)
+        return set_error(LPDEC_EINVAL, "lpdec_code_create: NULL index array");
+    if (row_ptr[0] != 0 || col_ptr[0] != 0)
+        return set_error(LPDEC_EINVAL, "lpdec_code_create: row_ptr[0] and col_ptr[0] must be 0");
+    int max_dc = 0;
+    for (int j = 0; j < m; ++j) {
+        const int d = row_ptr[j + 1] - row_ptr[j];
+        if (d < 1 || d > 32)
+            return set_error(LPDEC_EINVAL, "lpdec_code_create: check %d has degree %d (must be 1..32)", j, d);
+        max_dc = std::max(max_dc, d);
+    }
+    const int64_t E = row_ptr[m];
+    if (E > (int64_t)1 << 30) return set_error(LPDEC_EINVAL, "lpdec_code_create: too many edges");
+    if (col_ptr[n] != E) return set_error(LPDEC_EINVAL, "lpdec_code_create: col_ptr[n]=%d != E=%lld", col_ptr[n], (long long)E);
+    for (int j = 0; j < m; ++j)
+        for (int e = row_ptr[j]; e < row_ptr[j + 1]; ++e) {
+            if (col_idx[e] < 0 || col_idx[e] >= n)
+                return set_error(LPDEC_EINVAL, "lpdec_code_create: col_idx[%d]=%d out of range", e, col_idx[e]);
+            if (e > row_ptr[j] && col_idx[e] <= col_idx[e - 1])
+                return set_error(LPDEC_EINVAL, "lpdec_code_create: columns of check %d not strictly ascending", j);
+        }
+    for (int i = 0; i < n; ++i)
+        if (col_ptr[i + 1] < col_ptr[i] || col_ptr[i + 1] > E)
+            return set_error(LPDEC_EINVAL, "lpdec_code_create: col_ptr is not nondecreasing within [0, E]");
+    std::vector<int32_t> edge_row((size_t)E);
+    for (int j = 0; j < m; ++j)
+        for (int e = row_ptr[j]; e < row_ptr[j + 1]; ++e) edge_row[e] = j;
+    std::vector<uint8_t> seen((size_t)E, 0);
+    for (int i = 0; i < n; ++i) {
+        const int d = col_ptr[i + 1] - col_ptr[i];
+        if (d < 1) return set_error(LPDEC_EINVAL, "lpdec_code_create: variable %d has degree %d (must be >= 1)", i, d);
+        for (int s = col_ptr[i]; s < col_ptr[i + 1]; ++s) {
+            const int e = edge_perm[s];
+            if (e < 0 || e >= E || seen[e])
+                return set_error(LPDEC_EINVAL, "lpdec_code_create: edge_perm[%d]=%d invalid or repeated", s, e);
+            seen[e] = 1;
+            if (col_idx[e] != i || edge_row[e] != row_idx[s])
+                return set_error(LPDEC_EINVAL, "lpdec_code_create: CSC slot %d disagrees with CSR edge %d", s, e);
+            if (s > col_ptr[i] && row_idx[s] <= row_idx[s - 1])
+                return set_error(LPDEC_EINVAL, "lpdec_code_create: rows of variable %d not strictly ascending", i);
+        }
+    }
+
+    lpdec_code *c = new (std::nothrow) lpdec_code();
+    if (!c) return set_error(LPDEC_ENOMEM, "lpdec_code_create: host allocation failed");
+    c->n = n;
+    c->m = m;
+    c->E = (int)E;
+    c->Ep = (int)((E + 7) / 8 * 8);
+    c->max_dc = max_dc;
+    c->k_rank = gf2_k_rank(n, m, row_ptr, col_idx);
+    c->cls = lpdec::degree_class(max_dc);
+    cudaError_t err = cudaGetDevice(&c->device);
+    if (err != cudaSuccess) { delete c; return cuda_error(err, "lpdec_code_create: cudaGetDevice"); }
+    const size_t words = (size_t)(m + 1) + (size_t)E + (size_t)(n + 1) + (size_t)E;
+    err = cudaMalloc(&c->dev_block, words * sizeof(int32_t));
+    if (err != cudaSuccess) { delete c; return cuda_error(err, "lpdec_code_create: cudaMalloc"); }
+    int32_t *p = static_cast<int32_t *>(c->dev_block);
+    c->row_ptr = p;
+    c->col_idx = p + (m + 1);
+    c->col_ptr = c->col_idx + E;
+    c->csc_edge = c->col_ptr + (n + 1);
+    std::vector<int32_t> host;
+    host.reserve(words);
+    host.insert(host.end(), row_ptr, row_ptr + m + 1);
+    host.insert(host.end(), col_idx, col_idx + E);
+    host.insert(host.end(), col_ptr, col_ptr + n + 1);
+    host.insert(host.end(), edge_perm, edge_perm + E);
+    err = cudaMemcpy(c->dev_block, host.data(), words * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) {
+        cudaFree(c->dev_block);
+        delete c;
+        return cuda_error(err, "lpdec_code_create: cudaMemcpy");
+    }
+    *out = c;
+    return LPDEC_OK;
+}
+
+extern "C" int lpdec_code_info(const lpdec_code *c, int32_t *n, int32_t *m, int64_t *E, int32_t *max_dc,
+                               int32_t *k_rank) {
+    if (!c) return set_error(LPDEC_EINVAL, "lpdec_code_info: code is NULL");
+    if (n) *n = c->n;
+    if (m) *m = c->m;
+    if (E) *E = c->E;
+    if (max_dc) *max_dc = c->max_dc;
+    if (k_rank) *k_rank = c->k_rank;
+    return LPDEC_OK;
+}
+
+extern "C" int lpdec_code_destroy(lpdec_code *c) {
+    if (!c) return set_error(LPDEC_EINVAL, "lpdec_code_destroy: code is NULL");
+    cudaError_t err = cudaFree(c->dev_block);
+    delete c;
+    if (err != cudaSuccess) return cuda_error(err, "lpdec_code_destroy: cudaFree");
+    return LPDEC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// launch plumbing
+namespace lpdec {
+
+static cudaError_t class_prepare(int cls, int dtype, size_t smem) {
+    switch (kClassD[cls]) {
+        case 6: return prepare_decode_6(dtype, smem);
+        case 8: return prepare_decode_8(dtype, smem);
+        case 16: return prepare_decode_16(dtype, smem);
+        case 20: return prepare_decode_20(dtype, smem);
+        default: return prepare_decode_32(dtype, smem);
+    }
+}
+static cudaError_t class_occupancy(int cls, int dtype, int block, size_t smem, int *bps) {
+    switch (kClassD[cls]) {
+        case 6: return occupancy_decode_6(dtype, block, smem, bps);
+        case 8: return occupancy_decode_8(dtype, block, smem, bps);
+        case 16: return occupancy_decode_16(dtype, block, smem, bps);
+        case 20: return occupancy_decode_20(dtype, block, smem, bps);
+        default: return occupancy_decode_32(dtype, block, smem, bps);
+    }
+}
+static cudaError_t class_launch(int cls, int dtype, const DecodeArgs &a, const LaunchCfg &lc) {
+    switch (kClassD[cls]) {
+        case 6: return launch_decode_6(dtype, a, lc);
+        case 8: return launch_decode_8(dtype, a, lc);
+        case 16: return launch_decode_16(dtype, a, lc);
+        case 20: return launch_decode_20(dtype, a, lc);
+        default: return launch_decode_32(dtype, a, lc);
+    }
+}
+
+static size_t dtype_size(int dtype) { return dtype == LPDEC_STATE_F32 ? 4 : 2; }
+
+// Byte layout of one group's shared-memory slice (must match decode_kernel).
+SliceLayout slice_layout(const lpdec_code *c, int dtype, int group_threads) {
+    SliceLayout L;
+    size_t off = 2 * (size_t)c->Ep * dtype_size(dtype);
+    off = (off + 15) & ~(size_t)15;
+    L.off_x = off;
+    off += ((size_t)c->n * 4 + 15) & ~(size_t)15;
+    L.off_red = off;
+    off += (size_t)(group_threads / 32) * 2 * 4 + 8 * 4;
+    L.bytes = (off + 127) & ~(size_t)127;
+    return L;
+}
+
+int device_smem_optin(int device) {
+    static std::mutex mu;
+    static int cached[64] = {0};
+    std::lock_guard<std::mutex> lk(mu);
+    if (device < 0 || device >= 64) return 0;
+    if (!cached[device]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) v = 48 * 1024;
+        cached[device] = v;
+    }
+    return cached[device];
+}
+
+int device_sm_count(int device) {
+    static std::mutex mu;
+    static int cached[64] = {0};
+    std::lock_guard<std::mutex> lk(mu);
+    if (device < 0 || device >= 64) return 1;
+    if (!cached[device]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) v = 1;
+        cached[device] = v;
+    }
+    return cached[device];
+}
+
+// Default tile: groups of at most 256 threads (each thread owns one check per
+// pass), as many groups per CTA as threads, named barriers and shared memory
+// allow.  Several frames per SM keep warps busy across the group barriers.
+Tile default_tile(const lpdec_code *c, int dtype) {
+    Tile t;
+    const int maxT = class_max_threads(c->cls);
+    const int cap = std::min(256, maxT);
+    const int passes = (c->m + cap - 1) / cap;
+    int gt = ((c->m + passes - 1) / passes + 31) / 32 * 32;
+    gt = std::max(32, std::min(gt, cap));
+    const SliceLayout L = slice_layout(c, dtype, gt);
+    const int smem_cap = device_smem_optin(c->device);
+    int g = std::min(15, maxT / gt);
+    g = std::max(1, std::min<int>(g, (int)(smem_cap / std::max<size_t>(L.bytes, 1))));
+    t.group_threads = gt;
+    t.groups = g;
+    return t;
+}
+
+int plan_launch(const lpdec_code *c, int dtype, const Tile &tile, int n_frames, cudaStream_t stream,
+                LaunchCfg *lc, SliceLayout *layout) {
+    const SliceLayout L = slice_layout(c, dtype, tile.group_threads);
+    const size_t smem = L.bytes * (size_t)tile.groups;
+    if ((int)smem > device_smem_optin(c->device) || tile.groups < 1)
+        return set_error(LPDEC_EINVAL, "frame state (%zu bytes per group x %d groups) does not fit in shared memory (%d bytes)",
+                         L.bytes, tile.groups, device_smem_optin(c->device));
+    const int block = tile.groups * tile.group_threads;
+    if (block > class_max_threads(c->cls) || tile.groups > 15 || tile.group_threads % 32)
+        return set_error(LPDEC_EINVAL, "invalid tile: %d groups x %d threads", tile.groups, tile.group_threads);
+    cudaError_t err = class_prepare(c->cls, dtype, smem);
+    if (err != cudaSuccess) return cuda_error(err, "cudaFuncSetAttribute");
+    int bps = 0;
+    err = class_occupancy(c->cls, dtype, block, smem, &bps);
+    if (err != cudaSuccess) return cuda_error(err, "occupancy query");
+    if (bps < 1) return set_error(LPDEC_EINVAL, "tile does not fit on an SM (%d threads, %zu bytes)", block, smem);
+    const long long need = ((long long)n_frames + tile.groups - 1) / tile.groups;
+    const long long persistent = (long long)bps * device_sm_count(c->device);
+    lc->grid = (int)std::max<long long>(1, std::min(need, persistent));
+    lc->block = block;
+    lc->smem = smem;
+    lc->stream = stream;
+    if (layout) *layout = L;
+    return LPDEC_OK;
+}
+
+int validate_params(const lpdec_params *p) {
+    if (!p) return set_error(LPDEC_EINVAL, "params is NULL");
+    if (!(p->mu > 0.0) || !std::isfinite(p->mu)) return set_error(LPDEC_EINVAL, "mu=%g must be > 0", p->mu);
+    if (!(p->rho >= 1.0 && p->rho < 2.0)) return set_error(LPDEC_EINVAL, "rho=%g must be in [1, 2)", p->rho);
+    if (!(p->eps >= 0.0) || !std::isfinite(p->eps)) return set_error(LPDEC_EINVAL, "eps=%g must be >= 0", p->eps);
+    if (p->max_iter < 1) return set_error(LPDEC_EINVAL, "max_iter=%d must be >= 1", p->max_iter);
+    if (p->state_dtype < 0 || p->state_dtype > 2) return set_error(LPDEC_EINVAL, "unknown state_dtype %d", p->state_dtype);
+    if (!(p->cert_tol > 0.0 && p->cert_tol < 0.5)) return set_error(LPDEC_EINVAL, "cert_tol=%g must be in (0, 0.5)", p->cert_tol);
+    if (p->schedule < 0 || p->schedule > 2) return set_error(LPDEC_EINVAL, "unknown schedule %d", p->schedule);
+    if (p->iters_per_launch < 1) return set_error(LPDEC_EINVAL, "iters_per_launch=%d must be >= 1", p->iters_per_launch);
+    for (int i = 0; i < 6; ++i)
+        if (p->reserved[i]) return set_error(LPDEC_EINVAL, "reserved fields must be zero");
+    return LPDEC_OK;
+}
+
+IterCfg make_cfg(const lpdec_code *c, const lpdec_params *p) {
+    IterCfg cfg;
+    cfg.mu_inv = (float)(1.0 / p->mu);
+    cfg.rho = (float)p->rho;
+    cfg.omr = (float)(1.0 - p->rho);
+    cfg.cert_tol = (float)p->cert_tol;
+    cfg.eps2E = p->eps * p->eps * (double)c->E;
+    const double epsc = std::max(p->eps, 1e-5);
+    cfg.epsc2E = epsc * epsc * (double)c->E;
+    cfg.max_iter = p->max_iter;
+    cfg.check_stop = p->eps > 0.0 ? 1 : 0;
+    return cfg;
+}
+
+CodeView make_view(const lpdec_code *c) {
+    CodeView v;
+    v.n = c->n;
+    v.m = c->m;
+    v.E = c->E;
+    v.Ep = c->Ep;
+    v.row_ptr = c->row_ptr;
+    v.col_idx = c->col_idx;
+    v.col_ptr = c->col_ptr;
+    v.csc_edge = c->csc_edge;
+    return v;
+}
+
+// Enqueue the decode of n_frames frames.  `work` must hold workspace_bytes().
+size_t workspace_bytes(const lpdec_code *c, int n_frames, int schedule, int dtype, int max_iter, int ipl) {
+    size_t b = 256;  // queue counters for the launches, padded
+    const int launches = schedule == LPDEC_SCHED_STREAMED ? (max_iter + ipl - 1) / ipl : 1;
+    b += (size_t)launches * 4;
+    b = (b + 255) & ~(size_t)255;
+    if (schedule == LPDEC_SCHED_STREAMED) {
+        b += 2 * (size_t)n_frames * c->Ep * dtype_size(dtype);
+        b += ((size_t)n_frames * 4 + 255) & ~(size_t)255;
+    }
+    return b;
+}
+
+int resolve_schedule(const lpdec_code *c, const lpdec_params *p, const Tile &tile) {
+    if (p->schedule != LPDEC_SCHED_AUTO) return p->schedule;
+    const SliceLayout L = slice_layout(c, p->state_dtype, tile.group_threads);
+    return (int)L.bytes <= device_smem_optin(c->device) ? LPDEC_SCHED_RESIDENT : LPDEC_SCHED_STREAMED;
+}
+
+int enqueue_decode(const lpdec_code *c, int n_frames, const float *llr, const lpdec_params *p, float *x_out,
+                   uint8_t *bits_out, int32_t *iters_out, uint8_t *cert_out, cudaStream_t stream, void *work,
+                   int schedule, const Tile &tile_in, int *launches_out) {
+    Tile tile = tile_in;
+    LaunchCfg lc;
+    SliceLayout L;
+    int rc = plan_launch(c, p->state_dtype, tile, n_frames, stream, &lc, &L);
+    if (rc) return rc;
+    DecodeArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.code = make_view(c);
+    a.cfg = make_cfg(c, p);
+    a.n_frames = n_frames;
+    a.llr = llr;
+    a.x_out = x_out;
+    a.bits_out = bits_out;
+    a.iters_out = iters_out;
+    a.cert_out = cert_out;
+    a.group_threads = tile.group_threads;
+    a.smem_per_group = (int)L.bytes;
+    a.off_x = (int)L.off_x;
+    a.off_red = (int)L.off_red;
+    const int ipl = schedule == LPDEC_SCHED_STREAMED ? p->iters_per_launch : p->max_iter;
+    const int launches = schedule == LPDEC_SCHED_STREAMED ? (p->max_iter + ipl - 1) / ipl : 1;
+    char *w = static_cast<char *>(work);
+    int *queues = reinterpret_cast<int *>(w + 256);
+    size_t off = (256 + (size_t)launches * 4 + 255) & ~(size_t)255;
+    if (schedule == LPDEC_SCHED_STREAMED) {
+        const size_t sb = (size_t)n_frames * c->Ep * dtype_size(p->state_dtype);
+        a.z_state = w + off;
+        a.l_state = w + off + sb;
+        a.k_state = reinterpret_cast<int32_t *>(w + off + 2 * sb);
+        cudaError_t err = cudaMemsetAsync(a.k_state, 0, (size_t)n_frames * 4, stream);
+        if (err != cudaSuccess) return cuda_error(err, "cudaMemsetAsync");
+    }
+    cudaError_t err = cudaMemsetAsync(queues, 0, (size_t)launches * 4, stream);
+    if (err != cudaSuccess) return cuda_error(err, "cudaMemsetAsync");
+    a.iters_this_launch = ipl;
+    for (int L_ = 0; L_ < launches; ++L_) {
+        a.queue = queues + L_;
+        err = class_launch(c->cls, p->state_dtype, a, lc);
+        if (err != cudaSuccess) return cuda_error(err, "decode kernel launch");
+    }
+    if (launches_out) *launches_out = launches;
+    return LPDEC_OK;
+}
+
+}  // namespace lpdec
+
+// ---------------------------------------------------------------------------
+// decode entry points
+
+extern "C" int lpdec_decode(const lpdec_code *c, int32_t n_frames, const float *llr, const lpdec_params *p,
+                            float *x_out, uint8_t *bits_out, int32_t *iters_out, uint8_t *cert_out,
+                            void *cuda_stream) {
+    if (!c) return set_error(LPDEC_EINVAL, "lpdec_decode: code is NULL");
+    if (n_frames < 0) return set_error(LPDEC_EINVAL, "lpdec_decode: n_frames=%d < 0", n_frames);
+    int rc = lpdec::validate_params(p);
+    if (rc) return rc;
+    if (n_frames == 0) return LPDEC_OK;
+    if (!llr || !x_out) return set_error(LPDEC_EINVAL, "lpdec_decode: llr and x_out must not be NULL");
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    const lpdec::Tile tile = c->tuned[p->state_dtype].valid ? c->tuned[p->state_dtype] : lpdec::default_tile(c, p->state_dtype);
+    const int schedule = lpdec::resolve_schedule(c, p, tile);
+    const size_t wb = lpdec::workspace_bytes(c, n_frames, schedule, p->state_dtype, p->max_iter, p->iters_per_launch);
+    void *work = nullptr;
+    cudaError_t err = cudaMallocAsync(&work, wb, stream);
+    if (err != cudaSuccess) return cuda_error(err, "lpdec_decode: cudaMallocAsync of the workspace");
+    rc = lpdec::enqueue_decode(c, n_frames, llr, p, x_out, bits_out, iters_out, cert_out, stream, work, schedule,
+                               tile, nullptr);
+    err = cudaFreeAsync(work, stream);
+    if (rc) return rc;
+    if (err != cudaSuccess) return cuda_error(err, "lpdec_decode: cudaFreeAsync");
+    return LPDEC_OK;
+}
+
+extern "C" int lpdec_decode_host(const lpdec_code *c, int32_t n_frames, const float *llr, const lpdec_params *p,
+                                 float *x_out, uint8_t *bits_out, int32_t *iters_out, uint8_t *cert_out,
+                                 void *cuda_stream) {
+    if (!c) return set_error(LPDEC_EINVAL, "lpdec_decode_host: code is NULL");
+    if (n_frames < 0) return set_error(LPDEC_EINVAL, "lpdec_decode_host: n_frames=%d < 0", n_frames);
+    int rc = lpdec::validate_params(p);
+    if (rc) return rc;
+    if (n_frames == 0) return LPDEC_OK;
+    if (!llr || !x_out) return set_error(LPDEC_EINVAL, "lpdec_decode_host: llr and x_out must not be NULL");
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    const size_t nx = (size_t)n_frames * c->n;
+    const size_t bytes = nx * 4 /*llr*/ + nx * 4 /*x*/ + nx /*bits*/ + (size_t)n_frames * 5 + 4 * 256;
+    char *buf = nullptr;
+    cudaError_t err = cudaMallocAsync(reinterpret_cast<void **>(&buf), bytes, stream);
+    if (err != cudaSuccess) return cuda_error(err, "lpdec_decode_host: cudaMallocAsync");
+    auto align = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    float *d_llr = reinterpret_cast<float *>(buf);
+    float *d_x = reinterpret_cast<float *>(buf + align(nx * 4));
+    uint8_t *d_bits = reinterpret_cast<uint8_t *>(buf + align(nx * 4) + align(nx * 4));
+    int32_t *d_iters = reinterpret_cast<int32_t *>(buf + align(nx * 4) * 2 + align(nx));
+    uint8_t *d_cert = reinterpret_cast<uint8_t *>(buf + align(nx * 4) * 2 + align(nx) + align((size_t)n_frames * 4));
+    rc = LPDEC_OK;
+    err = cudaMemcpyAsync(d_llr, llr, nx * 4, cudaMemcpyHostToDevice, stream);
+    if (err != cudaSuccess) rc = cuda_error(err, "lpdec_decode_host: copy of llr");
+    if (!rc) rc = lpdec_decode(c, n_frames, d_llr, p, d_x, bits_out ? d_bits : nullptr, iters_out ? d_iters : nullptr,
+                               cert_out ? d_cert : nullptr, cuda_stream);
+    if (!rc) {
+        err = cudaMemcpyAsync(x_out, d_x, nx * 4, cudaMemcpyDeviceToHost, stream);
+        if (err == cudaSuccess && bits_out) err = cudaMemcpyAsync(bits_out, d_bits, nx, cudaMemcpyDeviceToHost, stream);
+        if (err == cudaSuccess && iters_out)
+            err = cudaMemcpyAsync(iters_out, d_iters, (size_t)n_frames * 4, cudaMemcpyDeviceToHost, stream);
+        if (err == cudaSuccess && cert_out)
+            err = cudaMemcpyAsync(cert_out, d_cert, (size_t)n_frames, cudaMemcpyDeviceToHost, stream);
+        if (err != cudaSuccess) rc = cuda_error(err, "lpdec_decode_host: copy of outputs");
+    }
+    cudaError_t e2 = cudaFreeAsync(buf, stream);
+    cudaError_t e3 = cudaStreamSynchronize(stream);
+    if (rc) return rc;
+    if (e2 != cudaSuccess) return cuda_error(e2, "lpdec_decode_host: cudaFreeAsync");
+    if (e3 != cudaSuccess) return cuda_error(e3, "lpdec_decode_host: cudaStreamSynchronize");
+    return LPDEC_OK;
+}
+
+extern "C" int lpdec_project(int32_t d, int64_t count, const float *v, float *z, void *cuda_stream) {
+    if (d < 1 || d > 32) return set_error(LPDEC_EINVAL, "lpdec_project: d=%d must be in [1, 32]", d);
+    if (count < 0) return set_error(LPDEC_EINVAL, "lpdec_project: count < 0");
+    if (count == 0) return LPDEC_OK;
+    if (!v || !z) return set_error(LPDEC_EINVAL, "lpdec_project: NULL pointer");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t err;
+    switch (lpdec::kClassD[lpdec::degree_class(d)]) {
+        case 6: err = lpdec::launch_project_6(d, count, v, z, s); break;
+        case 8: err = lpdec::launch_project_8(d, count, v, z, s); break;
+        case 16: err = lpdec::launch_project_16(d, count, v, z, s); break;
+        case 20: err = lpdec::launch_project_20(d, count, v, z, s); break;
+        default: err = lpdec::launch_project_32(d, count, v, z, s); break;
+    }
+    if (err != cudaSuccess) return cuda_error(err, "lpdec_project launch");
+    return LPDEC_OK;
+}

@@ -1,0 +1,50 @@
+// Host-side internals shared by the C-ABI translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "lpdec.h"
+#include "lpdec_internal.h"
+
+namespace lpdec {
+
+// Tile shape: `groups` frames decoded concurrently per CTA, each by a group of
+// `group_threads` threads (one check per thread per pass).
+struct Tile {
+    int groups = 1;
+    int group_threads = 32;
+    bool valid = false;  // set when chosen by the autotuner
+};
+
+struct SliceLayout {
+    size_t off_x = 0, off_red = 0, bytes = 0;
+};
+
+int set_error(int code, const char *fmt, ...);
+int cuda_error(cudaError_t e, const char *what);
+int validate_params(const lpdec_params *p);
+IterCfg make_cfg(const lpdec_code *c, const lpdec_params *p);
+CodeView make_view(const lpdec_code *c);
+SliceLayout slice_layout(const lpdec_code *c, int dtype, int group_threads);
+Tile default_tile(const lpdec_code *c, int dtype);
+int device_smem_optin(int device);
+int device_sm_count(int device);
+int plan_launch(const lpdec_code *c, int dtype, const Tile &tile, int n_frames, cudaStream_t stream,
+                LaunchCfg *lc, SliceLayout *layout);
+int resolve_schedule(const lpdec_code *c, const lpdec_params *p, const Tile &tile);
+size_t workspace_bytes(const lpdec_code *c, int n_frames, int schedule, int dtype, int max_iter, int ipl);
+int enqueue_decode(const lpdec_code *c, int n_frames, const float *llr, const lpdec_params *p, float *x_out,
+                   uint8_t *bits_out, int32_t *iters_out, uint8_t *cert_out, cudaStream_t stream, void *work,
+                   int schedule, const Tile &tile, int *launches_out);
+
+}  // namespace lpdec
+
+struct lpdec_code {
+    int n = 0, m = 0, E = 0, Ep = 0;
+    int max_dc = 0, k_rank = 0, cls = 0, device = 0;
+    void *dev_block = nullptr;  // one allocation holding the four index arrays
+    int32_t *row_ptr = nullptr, *col_idx = nullptr, *col_ptr = nullptr, *csc_edge = nullptr;
+    lpdec::Tile tuned[3];  // per state dtype, from lpdec_autotune
+};

@@ -1,0 +1,490 @@
+// Device code of liblpdec: the check-side projection onto the parity polytope
+// and the per-frame ADMM iteration (Algorithm 1, Section 3.3), for sm_103a.
+//
+// Work decomposition.  A *group* of GT threads (a whole number of warps)
+// decodes one frame at a time; a CTA holds G groups, each with its own slice
+// of shared memory and its own named barrier.  Inside a group:
+//   - variable phase: thread t owns variables t, t+GT, ...; it sums
+//     z_e - lambda_e/mu over the variable's edges (CSC order, gathered through
+//     the edge permutation) and writes x_i (Algorithm 1, x-update);
+//   - check phase: thread t owns checks t, t+GT, ...; it gathers x over the
+//     check's edges, forms the over-relaxed v, projects it onto PP_d in
+//     registers and writes z and lambda back (Algorithm 1, z- and
+//     lambda-updates);
+//   - stopping test: FP32 per-thread partials, FP32 warp shuffles, FP64 sum
+//     over the group's warps (the only FP64 on the GPU).
+// The z and lambda state is stored as S (float, bf16 or fp16); all
+// arithmetic is FP32.  lambda is kept pre-scaled as lambda/mu (the scaled
+// dual of Section 3.4), so the lambda-update is lambda' <- v - z.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace lpdec {
+
+constexpr float kPadV = -1.0e30f;  // value of an unused lane of a check (clips to 0)
+constexpr float kBigKappa = 1.0e30f;
+
+// ---------------------------------------------------------------------------
+// storage conversions
+template <typename S> __device__ __forceinline__ float ld(S v);
+template <> __device__ __forceinline__ float ld<float>(float v) { return v; }
+template <> __device__ __forceinline__ float ld<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <> __device__ __forceinline__ float ld<__half>(__half v) { return __half2float(v); }
+
+template <typename S> __device__ __forceinline__ S st(float v);
+template <> __device__ __forceinline__ float st<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 st<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <> __device__ __forceinline__ __half st<__half>(float v) { return __float2half_rn(v); }
+
+// ---------------------------------------------------------------------------
+// Batcher odd-even merge sort network (ascending) on a register array of N
+// values, N padded up to a power of two with +inf lanes whose comparators are
+// dropped (a comparator against +inf at the higher index never swaps).
+__host__ __device__ constexpr int pow2ceil(int n) { return n <= 1 ? 1 : 2 * pow2ceil((n + 1) / 2); }
+
+template <int N>
+__device__ __forceinline__ void sort_asc(float (&a)[N]) {
+    constexpr int P2 = pow2ceil(N);
+#pragma unroll
+    for (int p = 1; p < P2; p <<= 1) {
+#pragma unroll
+        for (int k = p; k >= 1; k >>= 1) {
+#pragma unroll
+            for (int j = k % p; j <= P2 - 1 - k; j += 2 * k) {
+#pragma unroll
+                for (int i = 0; i <= k - 1; ++i) {
+                    if ((i + j) / (p * 2) == (i + j + k) / (p * 2)) {
+                        const int lo = i + j, hi = i + j + k;
+                        if (hi < N) {
+                            const float x = a[lo], y = a[hi];
+                            a[lo] = fminf(x, y);
+                            a[hi] = fmaxf(x, y);
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// beta_opt of the two-slice projection.
+//
+// With S the odd set of the violated facet (f_k = +1 on S, -1 off S) and
+// kappa_k = v_k - 1 on S, kappa_k = -v_k off S (the breakpoints E1 and E2 of
+// Section 4.4), f^T clip(v - beta f) = |S| - 1 on the range where no entry
+// leaves the active set (Proposition in Section 4.4) reads
+//     sum_k max(0, beta - kappa_k) = 1,
+// a concave, decreasing, piecewise-linear equation whose root is
+//     beta* = min_m (1 + kappa_(1) + ... + kappa_(m)) / m
+// over the ascending order kappa_(1) <= kappa_(2) <= ...
+//
+// Small D: sort kappa with the network above, then take the minimum over m.
+template <int D>
+__device__ __forceinline__ float beta_sorted(float (&kap)[D], int d) {
+    sort_asc<D>(kap);
+    float P = 1.0f + kap[0];
+    float bn = P, bd = 1.0f;
+#pragma unroll
+    for (int m = 2; m <= D; ++m) {
+        P += kap[m - 1];
+        if (m <= d && P * bd < bn * (float)m) { bn = P; bd = (float)m; }
+    }
+    return fmaxf(__fdiv_rn(bn, bd), 0.0f);
+}
+
+// Michelot-style fixed point for large D (no sort, no kappa array): start
+// from all entries active and drop those with kappa >= beta until the active
+// set is stable.  The iterates decrease monotonically to beta* in at most d
+// passes.  kappa_k = v_k - 1 on the facet set (bit k of th), -v_k off it.
+template <int D>
+__device__ __forceinline__ float beta_fixed_point(const float (&v)[D], int d, unsigned th) {
+    float s = 1.0f;
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+        if (k < d) s += ((th >> k) & 1u) ? v[k] - 1.0f : -v[k];
+    float beta = __fdiv_rn(s, (float)d);
+    for (int it = 0; it < D; ++it) {
+        float s2 = 1.0f;
+        int cnt = 0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const float kap = ((th >> k) & 1u) ? v[k] - 1.0f : -v[k];
+            if (k < d && kap < beta) { s2 += kap; ++cnt; }
+        }
+        if (cnt == 0) break;
+        const float nb = __fdiv_rn(s2, (float)cnt);
+        if (!(nb < beta)) break;
+        beta = nb;
+    }
+    return fmaxf(beta, 0.0f);
+}
+
+// ---------------------------------------------------------------------------
+// Euclidean projection of v (entries k < d; entries k >= d must hold kPadV)
+// onto the parity polytope PP_d (Section 4.4, Algorithm 2).
+//
+//  1. cube clip zh = Pi_[0,1](v).
+//  2. the only odd-set facet sum_S z - sum_{S^c} z <= |S| - 1 that a cube
+//     point can violate is the most violated one: S = {k : zh_k > 1/2}, with
+//     the entry closest to 1/2 flipped when |S| is even.  When it is violated
+//     it is the facet f_r of eq. (fr-def) (S = the r+1 largest entries).
+//  3. not violated: zh is in PP_d (Corollary 1 / Lemma 4) and is the answer.
+//  4. violated: z = Pi_[0,1](v - beta* f_S) (Lemma 4) with beta* from the
+//     two-slice breakpoint equation above.
+//
+// The result is returned implicitly: z_k = Pi_[0,1](v_k - beta f_k) with
+// f_k = +1 where bit k of `facet` is set and -1 elsewhere; beta = 0 means
+// z = zh.  Callers form z on the fly, so no z array stays live.
+struct Proj {
+    unsigned facet;
+    float beta;
+};
+
+__device__ __forceinline__ float proj_z(float v, const Proj &pr, int k) {
+    return __saturatef(((pr.facet >> k) & 1u) ? v - pr.beta : v + pr.beta);
+}
+
+template <int D>
+__device__ __forceinline__ Proj project_pp(const float (&v)[D], int d) {
+    static_assert(D >= 1 && D <= 32, "check degree above 32");
+    unsigned th = 0u;
+    int kb = 0;
+    float best = 2.0f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        const float zh = __saturatef(v[k]);
+        if (zh > 0.5f) th |= 1u << k;
+        const float dist = fabsf(zh - 0.5f);
+        if (k < d && dist < best) { best = dist; kb = k; }
+    }
+    if ((__popc(th) & 1) == 0) th ^= 1u << kb;
+    const int s = __popc(th);
+    float g = 0.0f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        const float zh = __saturatef(v[k]);
+        g += ((th >> k) & 1u) ? zh : -zh;
+    }
+    Proj pr;
+    pr.facet = th;
+    pr.beta = 0.0f;
+    if (g <= (float)(s - 1)) return pr;  // zh already in PP_d
+
+    if constexpr (D <= 8) {
+        float kap[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k)
+            kap[k] = (k < d) ? (((th >> k) & 1u) ? v[k] - 1.0f : -v[k]) : kBigKappa;
+        pr.beta = beta_sorted<D>(kap, d);
+    } else {
+        pr.beta = beta_fixed_point<D>(v, d, th);
+    }
+    return pr;
+}
+
+// ---------------------------------------------------------------------------
+// Code graph and per-launch arguments (passed by value).
+struct CodeView {
+    int n, m, E, Ep;          // Ep: E rounded up to a multiple of 8 (state row stride)
+    const int *row_ptr;       // [m+1] CSR
+    const int *col_idx;       // [E]   variable of each CSR edge
+    const int *col_ptr;       // [n+1] CSC
+    const int *csc_edge;      // [E]   CSR edge id of each CSC slot
+};
+
+struct IterCfg {
+    float mu_inv;       // 1/mu
+    float rho;          // over-relaxation
+    float omr;          // 1 - rho
+    float cert_tol;
+    double eps2E;       // eps^2 * E
+    double epsc2E;      // max(eps, 1e-5)^2 * E
+    int max_iter;
+    int check_stop;     // eps > 0
+};
+
+struct DecodeArgs {
+    CodeView code;
+    IterCfg cfg;
+    int n_frames;
+    const float *llr;        // [F x n]
+    float *x_out;            // [F x n]
+    uint8_t *bits_out;       // [F x n] or null
+    int32_t *iters_out;      // [F] or null
+    uint8_t *cert_out;       // [F] or null
+    // STREAMED schedule: state kept in device memory between launches (null when RESIDENT)
+    void *z_state;           // [F x Ep] of S
+    void *l_state;           // [F x Ep] of S (lambda/mu)
+    int32_t *k_state;        // [F] iterations done; -1 once the frame is finished
+    int iters_this_launch;   // RESIDENT: max_iter
+    int *queue;              // frame work-queue counter, zero at launch
+    int group_threads;       // GT, a multiple of 32
+    int smem_per_group;      // bytes of one group's slice
+    int off_x;               // byte offset of x in a slice
+    int off_red;             // byte offset of the reduction scratch in a slice
+};
+
+// Named barrier for one group (ids 1..15; id 0 is __syncthreads).
+__device__ __forceinline__ void group_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+
+// One check update (Algorithm 1 z- and lambda-update with over-relaxation),
+// by one thread, in registers.  For small D the gathered x and old z stay in
+// registers; for large D they are re-read from shared memory in the store
+// pass to keep the register footprint at one D-array.
+template <int D, typename S>
+__device__ __forceinline__ void check_update(const CodeView &c, const IterCfg &p, int j,
+                                             S *zs, S *ls, const float *xs, bool need_res,
+                                             float &rp, float &rd) {
+    constexpr bool kKeep = D <= 8;
+    const int e0 = __ldg(c.row_ptr + j);
+    const int d = __ldg(c.row_ptr + j + 1) - e0;
+    float v[D];
+    float xv[kKeep ? D : 1], zo[kKeep ? D : 1];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        if (k < d) {
+            const int e = e0 + k;
+            const float xk = xs[__ldg(c.col_idx + e)];
+            const float zk = ld<S>(zs[e]);
+            if constexpr (kKeep) { xv[k] = xk; zo[k] = zk; }
+            const float q = fmaf(p.rho, xk, p.omr * zk);  // rho P_j x + (1 - rho) z_j^old
+            v[k] = q + ld<S>(ls[e]);                       // v_j = q + lambda_j / mu
+        } else {
+            v[k] = kPadV;
+        }
+    }
+    const Proj pr = project_pp<D>(v, d);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        if (k < d) {
+            const int e = e0 + k;
+            const float z = proj_z(v[k], pr, k);
+            float xk, zk;
+            if constexpr (kKeep) { xk = xv[k]; zk = zo[k]; }
+            else if (need_res) { xk = xs[__ldg(c.col_idx + e)]; zk = ld<S>(zs[e]); }
+            zs[e] = st<S>(z);
+            ls[e] = st<S>(v[k] - z);  // lambda/mu += q - z, i.e. lambda/mu = v - z
+            if (need_res) {
+                const float a = xk - z;
+                const float b = z - zk;
+                rp = fmaf(a, a, rp);
+                rd = fmaf(b, b, rd);
+            }
+        }
+    }
+}
+
+// Shared-memory slice of one group: z[Ep], l[Ep] (type S), x[n] (float),
+// red[2 * nwarps] (float), flags[8] (int).
+template <typename S>
+struct Slice {
+    S *z, *l;
+    float *x, *red;
+    int *flags;
+};
+
+// Copy nbytes (a multiple of 16) between 16-byte aligned buffers, cooperatively.
+__device__ __forceinline__ void copy16(void *dst, const void *src, int nbytes, int t, int T) {
+    uint4 *d = reinterpret_cast<uint4 *>(dst);
+    const uint4 *s = reinterpret_cast<const uint4 *>(src);
+    for (int i = t; i < (nbytes >> 4); i += T) d[i] = s[i];
+}
+__device__ __forceinline__ void zero16(void *dst, int nbytes, int t, int T) {
+    uint4 *d = reinterpret_cast<uint4 *>(dst);
+    const uint4 zz = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = t; i < (nbytes >> 4); i += T) d[i] = zz;
+}
+
+// Decode frame f (RESIDENT) or advance it by up to iters_this_launch
+// iterations (STREAMED), with one group of T threads; t is the thread's rank.
+// Every thread of the group calls this; all branches on shared data are
+// group-uniform.
+template <int D, typename S>
+__device__ void frame_run(const DecodeArgs &a, int f, const Slice<S> &sm, int t, int T, int bar) {
+    const CodeView &c = a.code;
+    const IterCfg &p = a.cfg;
+    const int lane = t & 31, w = t >> 5, nw = T >> 5;
+    volatile int *flags = sm.flags;
+    const float *gam = a.llr + (size_t)f * c.n;
+    const bool streamed = a.k_state != nullptr;
+    const int state_bytes = c.Ep * (int)sizeof(S);
+
+    int k = streamed ? a.k_state[f] : 0;
+    if (k < 0) return;  // finished in an earlier launch
+    if (t == 0) { flags[0] = 0; flags[1] = 0; flags[2] = 0; }
+
+    if (k == 0) {
+        // Algorithm 1 line 2: z = lambda = 0.  Also reject non-finite LLRs.
+        int bad = 0;
+        for (int i = t; i < c.n; i += T) bad |= !isfinite(__ldg(gam + i));
+        zero16(sm.z, 2 * state_bytes, t, T);
+        bad = __any_sync(0xffffffffu, bad);
+        group_sync(bar, T);
+        if (bad && lane == 0) atomicOr((int *)&flags[2], 1);
+        group_sync(bar, T);
+        if (flags[2]) {
+            float *xo = a.x_out + (size_t)f * c.n;
+            for (int i = t; i < c.n; i += T) {
+                xo[i] = 0.0f;
+                if (a.bits_out) a.bits_out[(size_t)f * c.n + i] = 0;
+            }
+            if (t == 0) {
+                if (a.iters_out) a.iters_out[f] = -1;
+                if (a.cert_out) a.cert_out[f] = 0;
+                if (streamed) a.k_state[f] = -1;
+            }
+            return;
+        }
+    } else {
+        const char *zg = reinterpret_cast<const char *>(a.z_state) + (size_t)f * state_bytes;
+        const char *lg = reinterpret_cast<const char *>(a.l_state) + (size_t)f * state_bytes;
+        copy16(sm.z, zg, state_bytes, t, T);
+        copy16(sm.l, lg, state_bytes, t, T);
+        group_sync(bar, T);
+    }
+
+    const int k_end = min(p.max_iter, k + a.iters_this_launch);
+    bool conv = false, rok = false;
+    while (k < k_end) {
+        // ---- x-update (Algorithm 1 lines 4-6; Section 3.2)
+        for (int i = t; i < c.n; i += T) {
+            const int s0 = __ldg(c.col_ptr + i), s1 = __ldg(c.col_ptr + i + 1);
+            float acc = 0.0f;
+            for (int s = s0; s < s1; ++s) {
+                const int e = __ldg(c.csc_edge + s);
+                acc += ld<S>(sm.z[e]) - ld<S>(sm.l[e]);
+            }
+            const float gi = __ldg(gam + i);
+            sm.x[i] = __saturatef((acc - gi * p.mu_inv) * __frcp_rn((float)(s1 - s0)));
+        }
+        group_sync(bar, T);
+        // ---- z- and lambda-updates (Algorithm 1 lines 7-11)
+        const bool need_res = p.check_stop || (k + 1 == p.max_iter);
+        float rp = 0.0f, rd = 0.0f;
+        for (int j = t; j < c.m; j += T) check_update<D, S>(c, p, j, sm.z, sm.l, sm.x, need_res, rp, rd);
+        ++k;
+        if (need_res) {
+            // ---- stopping test (Algorithm 1 line 13)
+            rp = warp_sum(rp);
+            rd = warp_sum(rd);
+            if (lane == 0) { sm.red[2 * w] = rp; sm.red[2 * w + 1] = rd; }
+            group_sync(bar, T);
+            if (t == 0) {
+                double Rp = 0.0, Rd = 0.0;
+                for (int q = 0; q < nw; ++q) { Rp += (double)sm.red[2 * q]; Rd += (double)sm.red[2 * q + 1]; }
+                flags[0] = (p.check_stop && Rp < p.eps2E && Rd < p.eps2E) ? 1 : 0;
+                flags[1] = (Rp < p.epsc2E && Rd < p.epsc2E) ? 1 : 0;
+            }
+            group_sync(bar, T);
+            conv = flags[0] != 0;
+            rok = flags[1] != 0;
+            if (conv) break;
+        } else {
+            group_sync(bar, T);
+        }
+    }
+
+    if (!conv && k < p.max_iter) {
+        // STREAMED: park the state in device memory for the next launch.
+        char *zg = reinterpret_cast<char *>(a.z_state) + (size_t)f * state_bytes;
+        char *lg = reinterpret_cast<char *>(a.l_state) + (size_t)f * state_bytes;
+        copy16(zg, sm.z, state_bytes, t, T);
+        copy16(lg, sm.l, state_bytes, t, T);
+        if (t == 0) a.k_state[f] = k;
+        return;
+    }
+
+    // ---- outputs: x, hard decision, certificate
+    float frac = 0.0f;
+    float *xo = a.x_out + (size_t)f * c.n;
+    uint8_t *bo = a.bits_out ? a.bits_out + (size_t)f * c.n : nullptr;
+    for (int i = t; i < c.n; i += T) {
+        const float x = sm.x[i];
+        xo[i] = x;
+        if (bo) bo[i] = x > 0.5f ? 1 : 0;
+        frac = fmaxf(frac, fminf(x, 1.0f - x));
+    }
+    int synd = 0;
+    for (int j = t; j < c.m; j += T) {
+        const int e0 = __ldg(c.row_ptr + j), e1 = __ldg(c.row_ptr + j + 1);
+        int par = 0;
+        for (int e = e0; e < e1; ++e) par ^= sm.x[__ldg(c.col_idx + e)] > 0.5f ? 1 : 0;
+        synd |= par;
+    }
+    frac = warp_max(frac);
+    synd = __any_sync(0xffffffffu, synd);
+    if (lane == 0) { sm.red[2 * w] = frac; sm.red[2 * w + 1] = synd ? 1.0f : 0.0f; }
+    group_sync(bar, T);
+    if (t == 0) {
+        float fr = 0.0f;
+        bool sy = false;
+        for (int q = 0; q < nw; ++q) { fr = fmaxf(fr, sm.red[2 * q]); sy |= sm.red[2 * q + 1] != 0.0f; }
+        if (a.iters_out) a.iters_out[f] = k;
+        if (a.cert_out) a.cert_out[f] = (rok && fr <= p.cert_tol && !sy) ? 1 : 0;
+        if (streamed) a.k_state[f] = -1;
+    }
+}
+
+// Persistent decode kernel: each group pulls frame ids from a global counter
+// until the batch is exhausted.  MAXT: largest CTA size the kernel is built for.
+template <int D, typename S, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) decode_kernel(const DecodeArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int T = a.group_threads;
+    const int g = threadIdx.x / T;
+    const int t = threadIdx.x - g * T;
+    const int bar = 1 + g;
+    unsigned char *base = smem_raw + (size_t)g * a.smem_per_group;
+    Slice<S> sm;
+    sm.z = reinterpret_cast<S *>(base);
+    sm.l = sm.z + a.code.Ep;
+    sm.x = reinterpret_cast<float *>(base + a.off_x);
+    sm.red = reinterpret_cast<float *>(base + a.off_red);
+    sm.flags = reinterpret_cast<int *>(sm.red + 2 * (T >> 5));
+    int par = 0;
+    for (;;) {
+        // frame ids are double-buffered (flags[4], flags[5]) so that a slow
+        // thread still reading this id is never overtaken by the next fetch
+        if (t == 0) sm.flags[4 + par] = atomicAdd(a.queue, 1);
+        group_sync(bar, T);
+        const int f = sm.flags[4 + par];
+        par ^= 1;
+        if (f >= a.n_frames) break;
+        frame_run<D, S>(a, f, sm, t, T, bar);
+    }
+}
+
+// Projection of `count` vectors of dimension d (d <= D), one per thread.
+template <int D>
+__global__ void __launch_bounds__(256) project_kernel(int d, long long count, const float *__restrict__ v,
+                                                     float *__restrict__ z) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    float vv[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) vv[k] = (k < d) ? v[i * d + k] : kPadV;
+    const Proj pr = project_pp<D>(vv, d);
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+        if (k < d) z[i * d + k] = proj_z(vv[k], pr, k);
+}
+
+}  // namespace lpdec

@@ -1,0 +1,46 @@
+// Internal interface between the C-ABI layer and the per-degree kernel units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "lpdec_device.cuh"
+
+namespace lpdec {
+
+// Degree classes: a check of degree d runs in the class D >= d (unused lanes
+// are padded).  D <= 8 sorts the breakpoints with a network; larger D uses
+// the sort-free fixed point.
+constexpr int kNumClasses = 5;
+constexpr int kClassD[kNumClasses] = {6, 8, 16, 20, 32};
+
+inline int degree_class(int max_dc) {
+    for (int i = 0; i < kNumClasses; ++i)
+        if (max_dc <= kClassD[i]) return i;
+    return -1;
+}
+
+// Largest CTA the decode kernel of a class is compiled for (register budget).
+inline int class_max_threads(int cls) { return kClassD[cls] <= 8 ? 1024 : 512; }
+
+struct LaunchCfg {
+    int grid;
+    int block;
+    size_t smem;
+    cudaStream_t stream;
+};
+
+// Per-class entry points, defined in lpdec_kD.cu.
+#define LPDEC_DECLARE_CLASS(D)                                                              \
+    cudaError_t launch_decode_##D(int dtype, const DecodeArgs &a, const LaunchCfg &lc);     \
+    cudaError_t occupancy_decode_##D(int dtype, int block, size_t smem, int *blocks_per_sm); \
+    cudaError_t prepare_decode_##D(int dtype, size_t smem);                                 \
+    cudaError_t launch_project_##D(int d, long long count, const float *v, float *z, cudaStream_t s);
+LPDEC_DECLARE_CLASS(6)
+LPDEC_DECLARE_CLASS(8)
+LPDEC_DECLARE_CLASS(16)
+LPDEC_DECLARE_CLASS(20)
+LPDEC_DECLARE_CLASS(32)
+#undef LPDEC_DECLARE_CLASS
+
+}  // namespace lpdec

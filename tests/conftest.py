@@ -21,3 +21,17 @@ def oracle_mod():
 
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def gpu():
+    """The CUDA library, built in-tree and loaded; fails (never skips) without a GPU."""
+    import torch
+
+    from paper_1204_0556_gb300 import build, lpdec
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+    lpdec.load()
+    torch.cuda.init()
+    return lpdec

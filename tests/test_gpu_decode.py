@@ -1,0 +1,233 @@
+"""GPU decoder (liblpdec through its C-ABI) vs the FP64 oracle, element by element.
+
+Tolerances: per-frame max|x - x_oracle| <= 1e-4 with FP32 state after a fixed
+iteration count (<= 5e-3 with 16-bit state); identical hard bits and
+certificates on every frame with no oracle entry within 1e-3 of 1/2 (or of the
+certificate tolerance); parity checks of the output compared bit-exactly.
+"""
+import numpy as np
+import pytest
+
+from paper_1204_0556_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+MU, RHO = 3.0, 1.9
+
+
+def gpu_decode(gpu, code, llr, **kw):
+    import torch
+
+    C = gpu.Code(code)
+    try:
+        p = gpu.make_params(**kw)
+        out = gpu.decode(C, torch.from_numpy(np.ascontiguousarray(llr, dtype=np.float32)).cuda(), p)
+        torch.cuda.synchronize()
+        return {k: v.cpu().numpy() for k, v in out.items()}
+    finally:
+        C.close()
+
+
+def oracle_decode(oracle_mod, code, llr, **kw):
+    kw = dict(kw)
+    kw.pop("state", None)
+    kw.pop("schedule", None)
+    kw.pop("iters_per_launch", None)
+    return oracle_mod.decode(code.row_ptr, code.col_idx, code.n, llr.astype(np.float64), **kw)
+
+
+def clean_frames(ref, cert_tol=1e-2):
+    x = ref["x"]
+    near_half = np.any(np.abs(x - 0.5) < 1e-3, axis=1)
+    frac = np.minimum(x, 1 - x).max(axis=1)
+    near_cert = np.abs(frac - cert_tol) < 1e-3
+    return ~(near_half | near_cert)
+
+
+def syndromes(code, bits):
+    H = code.dense().astype(np.int64)
+    return (bits.astype(np.int64) @ H.T) % 2
+
+
+def assert_parity(code, got, ref, xtol, same_iters=True):
+    if same_iters:
+        assert np.array_equal(got["iters"], ref["iters"])
+    err = np.abs(got["x"] - ref["x"]).max(axis=1)
+    assert err.max() <= xtol, (err.max(), int(np.argmax(err)))
+    clean = clean_frames(ref)
+    assert clean.mean() > 0.5
+    assert np.array_equal(got["bits"][clean], ref["bits"][clean])
+    assert np.array_equal(got["cert"][clean], ref["cert"][clean])
+    s_got, s_ref = syndromes(code, got["bits"]), syndromes(code, ref["bits"])
+    assert np.array_equal(s_got[clean], s_ref[clean])
+    # a certified GPU frame satisfies every check, recomputed bit-exactly on the host
+    assert not np.any(s_got[got["cert"] == 1])
+
+
+@pytest.fixture(scope="module")
+def c96():
+    return I.benchmark_code("C96", 0)
+
+
+@pytest.fixture(scope="module")
+def c1056():
+    return I.benchmark_code("C1056", 0)
+
+
+@pytest.mark.parametrize("schedule", ["resident", "streamed"])
+def test_c96_fixed_iterations(gpu, oracle_mod, c96, schedule):
+    llr = I.awgn_llr(c96, 2.0, 100, 1)
+    kw = dict(mu=MU, rho=RHO, eps=0.0, max_iter=200)
+    got = gpu_decode(gpu, c96, llr, schedule=schedule, **kw)
+    ref = oracle_decode(oracle_mod, c96, llr, **kw)
+    assert_parity(c96, got, ref, 1e-4)
+
+
+@pytest.mark.parametrize("schedule", ["resident", "streamed"])
+def test_c96_early_exit(gpu, oracle_mod, c96, schedule):
+    """The small FP64-reference configuration: (3,6) n=96, 2.0 dB, 100 frames of seed 1,
+    mu=3, rho=1.9, at most 200 iterations, eps=1e-5 (early exit per frame)."""
+    llr = I.awgn_llr(c96, 2.0, 100, 1)
+    kw = dict(mu=MU, rho=RHO, eps=1e-5, max_iter=200)
+    got = gpu_decode(gpu, c96, llr, schedule=schedule, **kw)
+    ref = oracle_decode(oracle_mod, c96, llr, **kw)
+    same = got["iters"] == ref["iters"]
+    assert same.mean() >= 0.9
+    assert np.abs(got["iters"] - ref["iters"]).max() <= 10
+    err = np.abs(got["x"] - ref["x"]).max(axis=1)
+    assert err[same].max() <= 1e-4
+    assert err.max() <= 1e-3
+    clean = clean_frames(ref)
+    assert np.array_equal(got["bits"][clean], ref["bits"][clean])
+    assert np.array_equal(got["cert"][clean], ref["cert"][clean])
+
+
+@pytest.mark.parametrize("schedule", ["resident", "streamed"])
+def test_c1056_fixed_300(gpu, oracle_mod, c1056, schedule):
+    llr = I.awgn_llr(c1056, 2.0, 160, 101)
+    kw = dict(mu=MU, rho=RHO, eps=0.0, max_iter=300)
+    got = gpu_decode(gpu, c1056, llr, schedule=schedule, **kw)
+    ref = oracle_decode(oracle_mod, c1056, llr, **kw)
+    assert_parity(c1056, got, ref, 1e-4)
+
+
+@pytest.mark.parametrize("state", ["bf16", "f16"])
+def test_16bit_state(gpu, oracle_mod, c1056, state):
+    llr = I.awgn_llr(c1056, 2.5, 160, 202)
+    kw = dict(mu=MU, rho=RHO, eps=0.0, max_iter=300)
+    got = gpu_decode(gpu, c1056, llr, state=state, **kw)
+    ref = oracle_decode(oracle_mod, c1056, llr, **kw)
+    err = np.abs(got["x"] - ref["x"]).max(axis=1)
+    print(f"{state}: max|x - x_oracle| = {err.max():.3e}, frames above 5e-3: {(err > 5e-3).sum()}")
+    assert err.max() <= 5e-3
+    clean = clean_frames(ref) & (err <= 5e-3)
+    assert np.array_equal(got["bits"][clean], ref["bits"][clean])
+
+
+@pytest.mark.parametrize("state", ["f32", "bf16", "f16"])
+def test_streamed_equals_resident(gpu, c1056, state):
+    llr = I.awgn_llr(c1056, 2.0, 50, 7)
+    a = gpu_decode(gpu, c1056, llr, eps=1e-5, max_iter=120, state=state, schedule="resident")
+    b = gpu_decode(gpu, c1056, llr, eps=1e-5, max_iter=120, state=state, schedule="streamed")
+    c = gpu_decode(gpu, c1056, llr, eps=1e-5, max_iter=120, state=state, schedule="streamed",
+                   iters_per_launch=7)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+        assert np.array_equal(a[k], c[k]), k
+
+
+@pytest.mark.parametrize("name,frames,iters", [("C2640", 8, 100), ("C4000", 8, 100), ("C8000", 6, 80)])
+def test_other_code_shapes(gpu, oracle_mod, name, frames, iters):
+    code = I.benchmark_code(name, 0)
+    llr = I.awgn_llr(code, 3.0, frames, 303)
+    kw = dict(mu=MU, rho=RHO, eps=0.0, max_iter=iters)
+    got = gpu_decode(gpu, code, llr, **kw)
+    ref = oracle_decode(oracle_mod, code, llr, **kw)
+    assert_parity(code, got, ref, 1e-4)
+
+
+def test_noiseless_all_zeros(gpu, c1056):
+    llr = np.full((5, c1056.n), 4.0, dtype=np.float32)
+    got = gpu_decode(gpu, c1056, llr, eps=1e-5, max_iter=100)
+    assert np.all(got["x"] == 0.0) and np.all(got["bits"] == 0)
+    assert np.all(got["iters"] == 1) and np.all(got["cert"] == 1)
+
+
+def test_ragged_batches_and_single_frame(gpu, oracle_mod, c96):
+    llr = I.awgn_llr(c96, 1.5, 37, 11)
+    kw = dict(mu=MU, rho=RHO, eps=0.0, max_iter=60)
+    ref = oracle_decode(oracle_mod, c96, llr, **kw)
+    for lo, hi in [(0, 37), (5, 6), (3, 20)]:
+        got = gpu_decode(gpu, c96, llr[lo:hi], **kw)
+        sub = {k: v[lo:hi] for k, v in ref.items()}
+        assert_parity(c96, got, sub, 1e-4)
+
+
+def test_bad_llr_frame_is_flagged(gpu, c96):
+    llr = I.awgn_llr(c96, 2.0, 4, 12)
+    llr[1, 7] = np.nan
+    llr[3, 0] = np.inf
+    got = gpu_decode(gpu, c96, llr, eps=1e-5, max_iter=50)
+    assert list(got["iters"][[1, 3]]) == [-1, -1]
+    assert got["cert"][1] == 0 and got["cert"][3] == 0
+    assert np.all(got["x"][1] == 0) and np.all(got["bits"][3] == 0)
+    assert got["iters"][0] >= 1 and got["iters"][2] >= 1
+
+
+def test_one_iteration(gpu, oracle_mod, c96):
+    llr = I.awgn_llr(c96, 2.0, 8, 13)
+    kw = dict(mu=MU, rho=RHO, eps=0.0, max_iter=1)
+    assert_parity(c96, gpu_decode(gpu, c96, llr, **kw), oracle_decode(oracle_mod, c96, llr, **kw), 1e-6)
+
+
+def test_low_degree_checks(gpu, oracle_mod):
+    """Degree-1 checks (PP_1 = {0}) and degree-2 checks (the diagonal of the square),
+    variables of degree 1, and a degree-5 check, in one small code."""
+    rows = [[0], [1, 2], [2, 3, 4], [0, 3, 5, 6, 7], [1, 6], [4, 5, 7]]
+    code = I.code_from_rows(8, rows)
+    llr = I.awgn_llr(code, 1.0, 40, 14)
+    kw = dict(mu=MU, rho=RHO, eps=0.0, max_iter=80)
+    assert_parity(code, gpu_decode(gpu, code, llr, **kw), oracle_decode(oracle_mod, code, llr, **kw), 1e-4)
+
+
+def test_zero_frames_is_a_noop(gpu, c96):
+    import torch
+
+    C = gpu.Code(c96)
+    try:
+        p = gpu.make_params()
+        gpu.lpdec_decode(C.handle, 0, 0, p, 0, 0, 0, 0, int(torch.cuda.current_stream().cuda_stream))
+    finally:
+        C.close()
+
+
+def test_host_entry_point_matches_device_entry(gpu, c96):
+    llr = I.awgn_llr(c96, 2.0, 20, 15)
+    a = gpu_decode(gpu, c96, llr, eps=1e-5, max_iter=100)
+    C = gpu.Code(c96)
+    try:
+        b = gpu.decode_host(C, llr, gpu.make_params(eps=1e-5, max_iter=100))
+    finally:
+        C.close()
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
+def _wilson(k, n, z=1.96):
+    p = k / n
+    den = 1 + z * z / n
+    c = (p + z * z / (2 * n)) / den
+    h = z * np.sqrt(p * (1 - p) / n + z * z / (4 * n * n)) / den
+    return c - h, c + h
+
+
+def test_wer_within_oracle_interval(gpu, oracle_mod, c1056):
+    llr = I.awgn_llr(c1056, 1.75, 1200, 404)
+    kw = dict(mu=MU, rho=RHO, eps=0.0, max_iter=300)
+    got = gpu_decode(gpu, c1056, llr, **kw)
+    ref = oracle_decode(oracle_mod, c1056, llr, **kw)
+    k_gpu = int((got["bits"].any(axis=1)).sum())
+    k_ref = int((ref["bits"].any(axis=1)).sum())
+    lo, hi = _wilson(k_ref, len(llr))
+    assert lo <= k_gpu / len(llr) <= hi, (k_gpu, k_ref)
+    assert k_ref >= 5
