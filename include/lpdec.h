@@ -166,6 +166,29 @@ LPDEC_API int lpdec_decode_host(const lpdec_code *code, int32_t n_frames, const 
                       int32_t *iters_out, uint8_t *cert_out, void *cuda_stream);
 
 /*
+ * As lpdec_decode, for callers that must not allocate device memory while they
+ * run (for example a receive loop with a fixed memory footprint and a latency
+ * budget that rules out allocator calls, or a host framework that owns all
+ * device memory and forbids side allocations).  The paper has no counterpart:
+ * this is a deployment variant of the same decode.
+ *   - Scratch space comes from one fixed 32 MiB device array inside the library
+ *     (held by every GPU that loads it, until the process exits) instead of
+ *     cudaMallocAsync; the call itself never allocates or frees.
+ *   - A decode that needs more scratch than 32 MiB is rejected with
+ *     LPDEC_ENOMEM before any work is queued.  RESIDENT decodes need under 1 KiB;
+ *     STREAMED decodes need about 2 * n_frames * E * (4 or 2) bytes.
+ *   - The first call on each device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - Every call reuses the same array and clears the parts that must start at
+ *     zero on its stream; two calls in flight on the GPU at the same time (on
+ *     different streams, or from different threads) race on it, so serialize them.
+ * Arguments, outputs and the other errors are those of lpdec_decode.
+ */
+LPDEC_API int lpdec_decode_noalloc(const lpdec_code *code, int32_t n_frames, const float *llr,
+                                   const lpdec_params *params, float *x_out, uint8_t *bits_out,
+                                   int32_t *iters_out, uint8_t *cert_out, void *cuda_stream);
+
+/*
  * Euclidean projection onto the parity polytope PP_d (Section 4.4, Algorithm 2)
  * of `count` vectors of dimension d, 1 <= d <= 32, computed exactly as the
  * decoder's check update computes it.

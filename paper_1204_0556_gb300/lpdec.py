@@ -36,7 +36,7 @@ _SCHEDS = {"auto": SCHED_AUTO, "streamed": SCHED_STREAMED, "resident": SCHED_RES
 EXPORTED = [
     "lpdec_params_default", "lpdec_last_error", "lpdec_version",
     "lpdec_code_create", "lpdec_code_info", "lpdec_code_destroy",
-    "lpdec_decode", "lpdec_decode_host", "lpdec_project",
+    "lpdec_decode", "lpdec_decode_host", "lpdec_project", "lpdec_decode_noalloc",
 ]
 
 
@@ -89,6 +89,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
             "lpdec_decode": (ctypes.c_int, [_vp, _i32, _vp, P, _vp, _vp, _vp, _vp, _vp]),
             "lpdec_decode_host": (ctypes.c_int, [_vp, _i32, _vp, P, _vp, _vp, _vp, _vp, _vp]),
             "lpdec_project": (ctypes.c_int, [_i32, _i64, _vp, _vp, _vp]),
+            "lpdec_decode_noalloc": (ctypes.c_int, [_vp, _i32, _vp, P, _vp, _vp, _vp, _vp, _vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -150,6 +151,14 @@ def lpdec_decode(handle, n_frames, llr_ptr, params, x_ptr, bits_ptr, iters_ptr, 
 def lpdec_decode_host(handle, n_frames, llr_ptr, params, x_ptr, bits_ptr, iters_ptr, cert_ptr, stream_ptr) -> None:
     _check(load().lpdec_decode_host(handle, n_frames, llr_ptr, ctypes.byref(params), x_ptr, bits_ptr, iters_ptr,
                                     cert_ptr, stream_ptr))
+
+
+def lpdec_decode_noalloc(handle, n_frames, llr_ptr, params, x_ptr, bits_ptr, iters_ptr, cert_ptr,
+                         stream_ptr) -> None:
+    """lpdec_decode with scratch in the library's fixed device array: no allocation
+    during the call (for callers that cannot allocate device memory as they run)."""
+    _check(load().lpdec_decode_noalloc(handle, n_frames, llr_ptr, ctypes.byref(params), x_ptr, bits_ptr,
+                                       iters_ptr, cert_ptr, stream_ptr))
 
 
 def lpdec_project(d, count, v_ptr, z_ptr, stream_ptr) -> None:
