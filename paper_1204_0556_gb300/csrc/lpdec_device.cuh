@@ -293,12 +293,13 @@ __device__ __forceinline__ void check_update(const CodeView &c, const IterCfg &p
 }
 
 // Shared-memory slice of one group: z[Ep], l[Ep] (type S), x[n] (float),
-// red[2 * nwarps] (float), flags[8] (int).
+// red[2 * nwarps] (float), flags[8] (int; the last two hold an mbarrier).
 template <typename S>
 struct Slice {
     S *z, *l;
     float *x, *red;
-    int *flags;
+    int *flags;      // [0] converged, [1] residual ok, [2] bad LLR, [3] copy ok, [4..5] frame ids
+    uint64_t *mbar;  // flags[6..7]: completion barrier of the bulk loads
 };
 
 // Copy nbytes (a multiple of 16) between 16-byte aligned buffers, cooperatively.
@@ -313,12 +314,70 @@ __device__ __forceinline__ void zero16(void *dst, int nbytes, int t, int T) {
     for (int i = t; i < (nbytes >> 4); i += T) d[i] = zz;
 }
 
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies (TMA engine, non-tensor form) between global and
+// shared memory, completed through an mbarrier (loads) or a bulk group
+// (stores).  Addresses must be 16-byte aligned and sizes multiples of 16.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for the mbarrier phase with the given parity, for at most ~1 s of SM
+// clocks; returns false on timeout (the caller reports it, never spins forever).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    const long long start = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - start > (1ll << 31)) return false;
+    }
+    return true;
+}
+__device__ __forceinline__ void bulk_load(void *dst_smem, const void *src_gmem, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst_smem)),
+        "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void bulk_store(void *dst_gmem, const void *src_smem, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst_gmem),
+                 "r"(smem_addr(src_smem)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Wait until every committed bulk store has finished reading shared memory.
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// Wait until every committed bulk store has completed.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// Order this thread's generic-proxy shared-memory accesses (and, after a
+// barrier, the group's) before later async-proxy accesses.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+constexpr int kFrameTimeout = -2;  // iters_out value of a frame abandoned after a copy timed out
+
 // Decode frame f (RESIDENT) or advance it by up to iters_this_launch
 // iterations (STREAMED), with one group of T threads; t is the thread's rank.
 // Every thread of the group calls this; all branches on shared data are
 // group-uniform.
+// Returns false only if a bulk copy timed out; the group must then stop.
 template <int D, typename S>
-__device__ void frame_run(const DecodeArgs &a, int f, const Slice<S> &sm, int t, int T, int bar) {
+__device__ bool frame_run(const DecodeArgs &a, int f, const Slice<S> &sm, int t, int T, int bar,
+                          uint32_t &phase) {
     const CodeView &c = a.code;
     const IterCfg &p = a.cfg;
     const int lane = t & 31, w = t >> 5, nw = T >> 5;
@@ -328,7 +387,7 @@ __device__ void frame_run(const DecodeArgs &a, int f, const Slice<S> &sm, int t,
     const int state_bytes = c.Ep * (int)sizeof(S);
 
     int k = streamed ? a.k_state[f] : 0;
-    if (k < 0) return;  // finished in an earlier launch
+    if (k < 0) return true;  // finished in an earlier launch
     if (t == 0) { flags[0] = 0; flags[1] = 0; flags[2] = 0; }
 
     if (k == 0) {
@@ -351,14 +410,31 @@ __device__ void frame_run(const DecodeArgs &a, int f, const Slice<S> &sm, int t,
                 if (a.cert_out) a.cert_out[f] = 0;
                 if (streamed) a.k_state[f] = -1;
             }
-            return;
+            return true;
         }
     } else {
+        // STREAMED: bring the parked z and lambda/mu back with two bulk copies.
         const char *zg = reinterpret_cast<const char *>(a.z_state) + (size_t)f * state_bytes;
         const char *lg = reinterpret_cast<const char *>(a.l_state) + (size_t)f * state_bytes;
-        copy16(sm.z, zg, state_bytes, t, T);
-        copy16(sm.l, lg, state_bytes, t, T);
+        if (t == 0) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(sm.mbar, 2u * (uint32_t)state_bytes);
+            bulk_load(sm.z, zg, (uint32_t)state_bytes, sm.mbar);
+            bulk_load(sm.l, lg, (uint32_t)state_bytes, sm.mbar);
+            flags[3] = mbar_wait_bounded(sm.mbar, phase) ? 1 : 0;
+        }
         group_sync(bar, T);
+        if (flags[3] == 0) {
+            if (t == 0) {
+                mbar_wait_bounded(sm.mbar, phase);  // one more bounded wait for the copies in flight
+                if (a.iters_out) a.iters_out[f] = kFrameTimeout;
+                if (a.cert_out) a.cert_out[f] = 0;
+                a.k_state[f] = -1;
+            }
+            return false;
+        }
+        mbar_wait_bounded(sm.mbar, phase);  // already complete: each thread acquires the copied data
+        phase ^= 1u;
     }
 
     const int k_end = min(p.max_iter, k + a.iters_this_launch);
@@ -403,13 +479,20 @@ __device__ void frame_run(const DecodeArgs &a, int f, const Slice<S> &sm, int t,
     }
 
     if (!conv && k < p.max_iter) {
-        // STREAMED: park the state in device memory for the next launch.
-        char *zg = reinterpret_cast<char *>(a.z_state) + (size_t)f * state_bytes;
-        char *lg = reinterpret_cast<char *>(a.l_state) + (size_t)f * state_bytes;
-        copy16(zg, sm.z, state_bytes, t, T);
-        copy16(lg, sm.l, state_bytes, t, T);
-        if (t == 0) a.k_state[f] = k;
-        return;
+        // STREAMED: park the state in device memory for the next launch with two
+        // bulk stores (the group barrier at the end of the iteration ordered every
+        // thread's shared-memory writes before them).  The next user of this
+        // slice waits for the stores to finish reading it.
+        if (t == 0) {
+            char *zg = reinterpret_cast<char *>(a.z_state) + (size_t)f * state_bytes;
+            char *lg = reinterpret_cast<char *>(a.l_state) + (size_t)f * state_bytes;
+            fence_proxy_async_smem();
+            bulk_store(zg, sm.z, (uint32_t)state_bytes);
+            bulk_store(lg, sm.l, (uint32_t)state_bytes);
+            bulk_commit();
+            a.k_state[f] = k;
+        }
+        return true;
     }
 
     // ---- outputs: x, hard decision, certificate
@@ -441,6 +524,7 @@ __device__ void frame_run(const DecodeArgs &a, int f, const Slice<S> &sm, int t,
         if (a.cert_out) a.cert_out[f] = (rok && fr <= p.cert_tol && !sy) ? 1 : 0;
         if (streamed) a.k_state[f] = -1;
     }
+    return true;
 }
 
 // Persistent decode kernel: each group pulls frame ids from a global counter
@@ -459,17 +543,29 @@ __global__ void __launch_bounds__(MAXT, 1) decode_kernel(const DecodeArgs a) {
     sm.x = reinterpret_cast<float *>(base + a.off_x);
     sm.red = reinterpret_cast<float *>(base + a.off_red);
     sm.flags = reinterpret_cast<int *>(sm.red + 2 * (T >> 5));
+    sm.mbar = reinterpret_cast<uint64_t *>(sm.flags + 6);
+    if (t == 0) {
+        mbar_init(sm.mbar, 1);
+        fence_proxy_async_smem();
+    }
+    uint32_t phase = 0;
     int par = 0;
     for (;;) {
         // frame ids are double-buffered (flags[4], flags[5]) so that a slow
-        // thread still reading this id is never overtaken by the next fetch
-        if (t == 0) sm.flags[4 + par] = atomicAdd(a.queue, 1);
+        // thread still reading this id is never overtaken by the next fetch.
+        // Before the slice is reused, the previous frame's bulk stores must
+        // have finished reading it.
+        if (t == 0) {
+            bulk_wait_read_all();
+            sm.flags[4 + par] = atomicAdd(a.queue, 1);
+        }
         group_sync(bar, T);
         const int f = sm.flags[4 + par];
         par ^= 1;
         if (f >= a.n_frames) break;
-        frame_run<D, S>(a, f, sm, t, T, bar);
+        if (!frame_run<D, S>(a, f, sm, t, T, bar, phase)) break;
     }
+    if (t == 0) bulk_wait_all();
 }
 
 // Projection of `count` vectors of dimension d (d <= D), one per thread.
