@@ -144,22 +144,33 @@ extern "C" int lpdec_code_create(int32_t n, int32_t m, const int32_t *row_ptr, c
     c->max_dc = max_dc;
     c->k_rank = gf2_k_rank(n, m, row_ptr, col_idx);
     c->cls = lpdec::degree_class(max_dc);
+    // Regular code whose check degree is exactly its class width: the decode
+    // kernel can then take edge offsets from j*D and i*DV.
+    {
+        bool reg = true;
+        const int dv0 = col_ptr[1] - col_ptr[0];
+        for (int j = 0; j < m && reg; ++j) reg = (row_ptr[j + 1] - row_ptr[j]) == lpdec::kClassD[c->cls];
+        for (int i = 0; i < n && reg; ++i) reg = (col_ptr[i + 1] - col_ptr[i]) == dv0;
+        c->reg_dv = reg ? dv0 : 0;
+    }
     cudaError_t err = cudaGetDevice(&c->device);
     if (err != cudaSuccess) { delete c; return cuda_error(err, "lpdec_code_create: cudaGetDevice"); }
-    const size_t words = (size_t)(m + 1) + (size_t)E + (size_t)(n + 1) + (size_t)E;
+    // Four index arrays in one allocation, each starting on a 16-byte boundary.
+    auto pad4 = [](size_t w) { return (w + 3) & ~(size_t)3; };
+    const size_t o_row = 0, o_col = pad4((size_t)m + 1), o_cptr = o_col + pad4((size_t)E),
+                 o_csc = o_cptr + pad4((size_t)n + 1), words = o_csc + pad4((size_t)E);
     err = cudaMalloc(&c->dev_block, words * sizeof(int32_t));
     if (err != cudaSuccess) { delete c; return cuda_error(err, "lpdec_code_create: cudaMalloc"); }
     int32_t *p = static_cast<int32_t *>(c->dev_block);
-    c->row_ptr = p;
-    c->col_idx = p + (m + 1);
-    c->col_ptr = c->col_idx + E;
-    c->csc_edge = c->col_ptr + (n + 1);
-    std::vector<int32_t> host;
-    host.reserve(words);
-    host.insert(host.end(), row_ptr, row_ptr + m + 1);
-    host.insert(host.end(), col_idx, col_idx + E);
-    host.insert(host.end(), col_ptr, col_ptr + n + 1);
-    host.insert(host.end(), edge_perm, edge_perm + E);
+    c->row_ptr = p + o_row;
+    c->col_idx = p + o_col;
+    c->col_ptr = p + o_cptr;
+    c->csc_edge = p + o_csc;
+    std::vector<int32_t> host(words, 0);
+    std::copy(row_ptr, row_ptr + m + 1, host.begin() + o_row);
+    std::copy(col_idx, col_idx + E, host.begin() + o_col);
+    std::copy(col_ptr, col_ptr + n + 1, host.begin() + o_cptr);
+    std::copy(edge_perm, edge_perm + E, host.begin() + o_csc);
     err = cudaMemcpy(c->dev_block, host.data(), words * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (err != cudaSuccess) {
         cudaFree(c->dev_block);
@@ -193,31 +204,31 @@ extern "C" int lpdec_code_destroy(lpdec_code *c) {
 // launch plumbing
 namespace lpdec {
 
-static cudaError_t class_prepare(int cls, int dtype, size_t smem) {
-    switch (kClassD[cls]) {
-        case 6: return prepare_decode_6(dtype, smem);
-        case 8: return prepare_decode_8(dtype, smem);
-        case 16: return prepare_decode_16(dtype, smem);
-        case 20: return prepare_decode_20(dtype, smem);
-        default: return prepare_decode_32(dtype, smem);
+static cudaError_t class_prepare(const lpdec_code *c, int dtype, size_t smem) {
+    switch (kClassD[c->cls]) {
+        case 6: return prepare_decode_6(dtype, c->reg_dv, smem);
+        case 8: return prepare_decode_8(dtype, c->reg_dv, smem);
+        case 16: return prepare_decode_16(dtype, c->reg_dv, smem);
+        case 20: return prepare_decode_20(dtype, c->reg_dv, smem);
+        default: return prepare_decode_32(dtype, c->reg_dv, smem);
     }
 }
-static cudaError_t class_occupancy(int cls, int dtype, int block, size_t smem, int *bps) {
-    switch (kClassD[cls]) {
-        case 6: return occupancy_decode_6(dtype, block, smem, bps);
-        case 8: return occupancy_decode_8(dtype, block, smem, bps);
-        case 16: return occupancy_decode_16(dtype, block, smem, bps);
-        case 20: return occupancy_decode_20(dtype, block, smem, bps);
-        default: return occupancy_decode_32(dtype, block, smem, bps);
+static cudaError_t class_occupancy(const lpdec_code *c, int dtype, int block, size_t smem, int *bps) {
+    switch (kClassD[c->cls]) {
+        case 6: return occupancy_decode_6(dtype, c->reg_dv, block, smem, bps);
+        case 8: return occupancy_decode_8(dtype, c->reg_dv, block, smem, bps);
+        case 16: return occupancy_decode_16(dtype, c->reg_dv, block, smem, bps);
+        case 20: return occupancy_decode_20(dtype, c->reg_dv, block, smem, bps);
+        default: return occupancy_decode_32(dtype, c->reg_dv, block, smem, bps);
     }
 }
-static cudaError_t class_launch(int cls, int dtype, const DecodeArgs &a, const LaunchCfg &lc) {
-    switch (kClassD[cls]) {
-        case 6: return launch_decode_6(dtype, a, lc);
-        case 8: return launch_decode_8(dtype, a, lc);
-        case 16: return launch_decode_16(dtype, a, lc);
-        case 20: return launch_decode_20(dtype, a, lc);
-        default: return launch_decode_32(dtype, a, lc);
+static cudaError_t class_launch(const lpdec_code *c, int dtype, const DecodeArgs &a, const LaunchCfg &lc) {
+    switch (kClassD[c->cls]) {
+        case 6: return launch_decode_6(dtype, c->reg_dv, a, lc);
+        case 8: return launch_decode_8(dtype, c->reg_dv, a, lc);
+        case 16: return launch_decode_16(dtype, c->reg_dv, a, lc);
+        case 20: return launch_decode_20(dtype, c->reg_dv, a, lc);
+        default: return launch_decode_32(dtype, c->reg_dv, a, lc);
     }
 }
 
@@ -291,10 +302,10 @@ int plan_launch(const lpdec_code *c, int dtype, const Tile &tile, int n_frames, 
     const int block = tile.groups * tile.group_threads;
     if (block > class_max_threads(c->cls) || tile.groups > 15 || tile.group_threads % 32)
         return set_error(LPDEC_EINVAL, "invalid tile: %d groups x %d threads", tile.groups, tile.group_threads);
-    cudaError_t err = class_prepare(c->cls, dtype, smem);
+    cudaError_t err = class_prepare(c, dtype, smem);
     if (err != cudaSuccess) return cuda_error(err, "cudaFuncSetAttribute");
     int bps = 0;
-    err = class_occupancy(c->cls, dtype, block, smem, &bps);
+    err = class_occupancy(c, dtype, block, smem, &bps);
     if (err != cudaSuccess) return cuda_error(err, "occupancy query");
     if (bps < 1) return set_error(LPDEC_EINVAL, "tile does not fit on an SM (%d threads, %zu bytes)", block, smem);
     const long long need = ((long long)n_frames + tile.groups - 1) / tile.groups;
@@ -408,7 +419,7 @@ int enqueue_decode(const lpdec_code *c, int n_frames, const float *llr, const lp
     a.iters_this_launch = ipl;
     for (int L_ = 0; L_ < launches; ++L_) {
         a.queue = queues + L_;
-        err = class_launch(c->cls, p->state_dtype, a, lc);
+        err = class_launch(c, p->state_dtype, a, lc);
         if (err != cudaSuccess) return cuda_error(err, "decode kernel launch");
     }
     if (launches_out) *launches_out = launches;

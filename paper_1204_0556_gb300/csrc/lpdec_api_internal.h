@@ -44,6 +44,7 @@ int enqueue_decode(const lpdec_code *c, int n_frames, const float *llr, const lp
 struct lpdec_code {
     int n = 0, m = 0, E = 0, Ep = 0;
     int max_dc = 0, k_rank = 0, cls = 0, device = 0;
+    int reg_dv = 0;             // variable degree if the code is regular with check degree == class D, else 0
     void *dev_block = nullptr;  // one allocation holding the four index arrays
     int32_t *row_ptr = nullptr, *col_idx = nullptr, *col_ptr = nullptr, *csc_edge = nullptr;
     lpdec::Tile tuned[3];  // per state dtype, from lpdec_autotune

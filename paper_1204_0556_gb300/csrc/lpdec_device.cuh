@@ -39,6 +39,26 @@ template <> __device__ __forceinline__ float st<float>(float v) { return v; }
 template <> __device__ __forceinline__ __nv_bfloat16 st<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 template <> __device__ __forceinline__ __half st<__half>(float v) { return __float2half_rn(v); }
 
+// Two adjacent state elements (for even-aligned pairs of edges of a check).
+template <typename S> __device__ __forceinline__ float2 ld2(const S *p);
+template <> __device__ __forceinline__ float2 ld2<float>(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+template <> __device__ __forceinline__ float2 ld2<__half>(const __half *p) {
+    return __half22float2(*reinterpret_cast<const __half2 *>(p));
+}
+template <> __device__ __forceinline__ float2 ld2<__nv_bfloat16>(const __nv_bfloat16 *p) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+}
+template <typename S> __device__ __forceinline__ void st2(S *p, float a, float b);
+template <> __device__ __forceinline__ void st2<float>(float *p, float a, float b) {
+    *reinterpret_cast<float2 *>(p) = make_float2(a, b);
+}
+template <> __device__ __forceinline__ void st2<__half>(__half *p, float a, float b) {
+    *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a, b);
+}
+template <> __device__ __forceinline__ void st2<__nv_bfloat16>(__nv_bfloat16 *p, float a, float b) {
+    *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
+}
+
 // ---------------------------------------------------------------------------
 // Batcher odd-even merge sort network (ascending) on a register array of N
 // values, N padded up to a power of two with +inf lanes whose comparators are
@@ -93,7 +113,7 @@ __device__ __forceinline__ float beta_sorted(float (&kap)[D], int d) {
         P += kap[m - 1];
         if (m <= d && P * bd < bn * (float)m) { bn = P; bd = (float)m; }
     }
-    return fmaxf(__fdiv_rn(bn, bd), 0.0f);
+    return fmaxf(__fdividef(bn, bd), 0.0f);
 }
 
 // Michelot-style fixed point for large D (no sort, no kappa array): start
@@ -106,7 +126,7 @@ __device__ __forceinline__ float beta_fixed_point(const float (&v)[D], int d, un
 #pragma unroll
     for (int k = 0; k < D; ++k)
         if (k < d) s += ((th >> k) & 1u) ? v[k] - 1.0f : -v[k];
-    float beta = __fdiv_rn(s, (float)d);
+    float beta = __fdividef(s, (float)d);
     for (int it = 0; it < D; ++it) {
         float s2 = 1.0f;
         int cnt = 0;
@@ -116,7 +136,7 @@ __device__ __forceinline__ float beta_fixed_point(const float (&v)[D], int d, un
             if (k < d && kap < beta) { s2 += kap; ++cnt; }
         }
         if (cnt == 0) break;
-        const float nb = __fdiv_rn(s2, (float)cnt);
+        const float nb = __fdividef(s2, (float)cnt);
         if (!(nb < beta)) break;
         beta = nb;
     }
@@ -249,44 +269,81 @@ __device__ __forceinline__ float warp_max(float v) {
 // by one thread, in registers.  For small D the gathered x and old z stay in
 // registers; for large D they are re-read from shared memory in the store
 // pass to keep the register footprint at one D-array.
-template <int D, typename S>
+// DV > 0: the code is regular (every check has degree D, so check j owns
+// edges j*D .. j*D+D-1, and every variable has degree DV); the edge state of a
+// check is then read and written in aligned pairs.
+template <int D, int DV, typename S>
 __device__ __forceinline__ void check_update(const CodeView &c, const IterCfg &p, int j,
                                              S *zs, S *ls, const float *xs, bool need_res,
                                              float &rp, float &rd) {
     constexpr bool kKeep = D <= 8;
-    const int e0 = __ldg(c.row_ptr + j);
-    const int d = __ldg(c.row_ptr + j + 1) - e0;
+    constexpr bool kReg = DV > 0;
+    constexpr bool kPairs = kReg && (D % 2 == 0);
+    const int e0 = kReg ? j * D : __ldg(c.row_ptr + j);
+    const int d = kReg ? D : __ldg(c.row_ptr + j + 1) - e0;
     float v[D];
     float xv[kKeep ? D : 1], zo[kKeep ? D : 1];
+    if constexpr (kPairs) {
+        const int2 *ci = reinterpret_cast<const int2 *>(c.col_idx + e0);
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-        if (k < d) {
-            const int e = e0 + k;
-            const float xk = xs[__ldg(c.col_idx + e)];
-            const float zk = ld<S>(zs[e]);
-            if constexpr (kKeep) { xv[k] = xk; zo[k] = zk; }
-            const float q = fmaf(p.rho, xk, p.omr * zk);  // rho P_j x + (1 - rho) z_j^old
-            v[k] = q + ld<S>(ls[e]);                       // v_j = q + lambda_j / mu
-        } else {
-            v[k] = kPadV;
+        for (int k = 0; k < D; k += 2) {
+            const int2 cc = __ldg(ci + k / 2);
+            const float x0 = xs[cc.x], x1 = xs[cc.y];
+            const float2 z2 = ld2<S>(zs + e0 + k);
+            const float2 l2 = ld2<S>(ls + e0 + k);
+            if constexpr (kKeep) { xv[k] = x0; xv[k + 1] = x1; zo[k] = z2.x; zo[k + 1] = z2.y; }
+            v[k] = fmaf(p.rho, x0, p.omr * z2.x) + l2.x;
+            v[k + 1] = fmaf(p.rho, x1, p.omr * z2.y) + l2.y;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            if (k < d) {
+                const int e = e0 + k;
+                const float xk = xs[__ldg(c.col_idx + e)];
+                const float zk = ld<S>(zs[e]);
+                if constexpr (kKeep) { xv[k] = xk; zo[k] = zk; }
+                const float q = fmaf(p.rho, xk, p.omr * zk);  // rho P_j x + (1 - rho) z_j^old
+                v[k] = q + ld<S>(ls[e]);                       // v_j = q + lambda_j / mu
+            } else {
+                v[k] = kPadV;
+            }
         }
     }
     const Proj pr = project_pp<D>(v, d);
+    if constexpr (kPairs) {
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-        if (k < d) {
-            const int e = e0 + k;
-            const float z = proj_z(v[k], pr, k);
-            float xk, zk;
-            if constexpr (kKeep) { xk = xv[k]; zk = zo[k]; }
-            else if (need_res) { xk = xs[__ldg(c.col_idx + e)]; zk = ld<S>(zs[e]); }
-            zs[e] = st<S>(z);
-            ls[e] = st<S>(v[k] - z);  // lambda/mu += q - z, i.e. lambda/mu = v - z
+        for (int k = 0; k < D; k += 2) {
+            const float z0 = proj_z(v[k], pr, k), z1 = proj_z(v[k + 1], pr, k + 1);
+            st2<S>(zs + e0 + k, z0, z1);
+            st2<S>(ls + e0 + k, v[k] - z0, v[k + 1] - z1);  // lambda/mu = v - z
             if (need_res) {
-                const float a = xk - z;
-                const float b = z - zk;
+                float a = xv[k] - z0, b = z0 - zo[k];
                 rp = fmaf(a, a, rp);
                 rd = fmaf(b, b, rd);
+                a = xv[k + 1] - z1;
+                b = z1 - zo[k + 1];
+                rp = fmaf(a, a, rp);
+                rd = fmaf(b, b, rd);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            if (k < d) {
+                const int e = e0 + k;
+                const float z = proj_z(v[k], pr, k);
+                float xk = 0.0f, zk = 0.0f;
+                if constexpr (kKeep) { xk = xv[k]; zk = zo[k]; }
+                else if (need_res) { xk = xs[__ldg(c.col_idx + e)]; zk = ld<S>(zs[e]); }
+                zs[e] = st<S>(z);
+                ls[e] = st<S>(v[k] - z);  // lambda/mu += q - z, i.e. lambda/mu = v - z
+                if (need_res) {
+                    const float a = xk - z;
+                    const float b = z - zk;
+                    rp = fmaf(a, a, rp);
+                    rd = fmaf(b, b, rd);
+                }
             }
         }
     }
@@ -375,7 +432,7 @@ constexpr int kFrameTimeout = -2;  // iters_out value of a frame abandoned after
 // Every thread of the group calls this; all branches on shared data are
 // group-uniform.
 // Returns false only if a bulk copy timed out; the group must then stop.
-template <int D, typename S>
+template <int D, int DV, typename S>
 __device__ bool frame_run(const DecodeArgs &a, int f, const Slice<S> &sm, int t, int T, int bar,
                           uint32_t &phase) {
     const CodeView &c = a.code;
@@ -442,20 +499,30 @@ __device__ bool frame_run(const DecodeArgs &a, int f, const Slice<S> &sm, int t,
     while (k < k_end) {
         // ---- x-update (Algorithm 1 lines 4-6; Section 3.2)
         for (int i = t; i < c.n; i += T) {
-            const int s0 = __ldg(c.col_ptr + i), s1 = __ldg(c.col_ptr + i + 1);
-            float acc = 0.0f;
-            for (int s = s0; s < s1; ++s) {
-                const int e = __ldg(c.csc_edge + s);
-                acc += ld<S>(sm.z[e]) - ld<S>(sm.l[e]);
+            float acc = 0.0f, inv_dv;
+            if constexpr (DV > 0) {
+#pragma unroll
+                for (int s = 0; s < DV; ++s) {
+                    const int e = __ldg(c.csc_edge + i * DV + s);
+                    acc += ld<S>(sm.z[e]) - ld<S>(sm.l[e]);
+                }
+                inv_dv = 1.0f / (float)DV;
+            } else {
+                const int s0 = __ldg(c.col_ptr + i), s1 = __ldg(c.col_ptr + i + 1);
+                for (int s = s0; s < s1; ++s) {
+                    const int e = __ldg(c.csc_edge + s);
+                    acc += ld<S>(sm.z[e]) - ld<S>(sm.l[e]);
+                }
+                inv_dv = __frcp_rn((float)(s1 - s0));
             }
             const float gi = __ldg(gam + i);
-            sm.x[i] = __saturatef((acc - gi * p.mu_inv) * __frcp_rn((float)(s1 - s0)));
+            sm.x[i] = __saturatef((acc - gi * p.mu_inv) * inv_dv);
         }
         group_sync(bar, T);
         // ---- z- and lambda-updates (Algorithm 1 lines 7-11)
         const bool need_res = p.check_stop || (k + 1 == p.max_iter);
         float rp = 0.0f, rd = 0.0f;
-        for (int j = t; j < c.m; j += T) check_update<D, S>(c, p, j, sm.z, sm.l, sm.x, need_res, rp, rd);
+        for (int j = t; j < c.m; j += T) check_update<D, DV, S>(c, p, j, sm.z, sm.l, sm.x, need_res, rp, rd);
         ++k;
         if (need_res) {
             // ---- stopping test (Algorithm 1 line 13)
@@ -528,8 +595,9 @@ __device__ bool frame_run(const DecodeArgs &a, int f, const Slice<S> &sm, int t,
 }
 
 // Persistent decode kernel: each group pulls frame ids from a global counter
-// until the batch is exhausted.  MAXT: largest CTA size the kernel is built for.
-template <int D, typename S, int MAXT>
+// until the batch is exhausted.  DV > 0 selects the regular-code form (check
+// degree D, variable degree DV).  MAXT: largest CTA size the kernel is built for.
+template <int D, int DV, typename S, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) decode_kernel(const DecodeArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int T = a.group_threads;
@@ -563,7 +631,7 @@ __global__ void __launch_bounds__(MAXT, 1) decode_kernel(const DecodeArgs a) {
         const int f = sm.flags[4 + par];
         par ^= 1;
         if (f >= a.n_frames) break;
-        if (!frame_run<D, S>(a, f, sm, t, T, bar, phase)) break;
+        if (!frame_run<D, DV, S>(a, f, sm, t, T, bar, phase)) break;
     }
     if (t == 0) bulk_wait_all();
 }

@@ -31,10 +31,12 @@ struct LaunchCfg {
 };
 
 // Per-class entry points, defined in lpdec_kD.cu.
-#define LPDEC_DECLARE_CLASS(D)                                                              \
-    cudaError_t launch_decode_##D(int dtype, const DecodeArgs &a, const LaunchCfg &lc);     \
-    cudaError_t occupancy_decode_##D(int dtype, int block, size_t smem, int *blocks_per_sm); \
-    cudaError_t prepare_decode_##D(int dtype, size_t smem);                                 \
+// reg_dv: the code's variable degree when it is regular with check degree
+// exactly D (selects the regular-code kernel where one is built), else 0.
+#define LPDEC_DECLARE_CLASS(D)                                                                           \
+    cudaError_t launch_decode_##D(int dtype, int reg_dv, const DecodeArgs &a, const LaunchCfg &lc);      \
+    cudaError_t occupancy_decode_##D(int dtype, int reg_dv, int block, size_t smem, int *blocks_per_sm); \
+    cudaError_t prepare_decode_##D(int dtype, int reg_dv, size_t smem);                                  \
     cudaError_t launch_project_##D(int d, long long count, const float *v, float *z, cudaStream_t s);
 LPDEC_DECLARE_CLASS(6)
 LPDEC_DECLARE_CLASS(8)

@@ -15,43 +15,58 @@ namespace lpdec {
 namespace {
 constexpr int kD = LPDEC_D;
 constexpr int kMaxT = kD <= 8 ? 1024 : 512;
+// Variable degree of the regular-code kernel built for this class (0: none).
+constexpr int kRegDV = kD == 6 ? 3 : (kD == 8 ? 4 : 0);
 
-template <typename S>
+template <int DV, typename S>
 const void *decode_fn() {
-    return reinterpret_cast<const void *>(&decode_kernel<kD, S, kMaxT>);
+    return reinterpret_cast<const void *>(&decode_kernel<kD, DV, S, kMaxT>);
 }
 
-const void *decode_fn_for(int dtype) {
+template <int DV>
+const void *decode_fn_dtype(int dtype) {
     switch (dtype) {
-        case 0: return decode_fn<float>();
-        case 1: return decode_fn<__nv_bfloat16>();
-        case 2: return decode_fn<__half>();
+        case 0: return decode_fn<DV, float>();
+        case 1: return decode_fn<DV, __nv_bfloat16>();
+        case 2: return decode_fn<DV, __half>();
         default: return nullptr;
     }
 }
+
+const void *decode_fn_for(int dtype, int reg_dv) {
+    if (kRegDV > 0 && reg_dv == kRegDV) return decode_fn_dtype<kRegDV>(dtype);
+    return decode_fn_dtype<0>(dtype);
+}
+
+template <int DV>
+cudaError_t launch_dv(int dtype, const DecodeArgs &a, const LaunchCfg &lc) {
+    switch (dtype) {
+        case 0: decode_kernel<kD, DV, float, kMaxT><<<lc.grid, lc.block, lc.smem, lc.stream>>>(a); break;
+        case 1: decode_kernel<kD, DV, __nv_bfloat16, kMaxT><<<lc.grid, lc.block, lc.smem, lc.stream>>>(a); break;
+        case 2: decode_kernel<kD, DV, __half, kMaxT><<<lc.grid, lc.block, lc.smem, lc.stream>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
 }  // namespace
 
-cudaError_t LPDEC_CAT(prepare_decode_, LPDEC_D)(int dtype, size_t smem) {
-    const void *fn = decode_fn_for(dtype);
+cudaError_t LPDEC_CAT(prepare_decode_, LPDEC_D)(int dtype, int reg_dv, size_t smem) {
+    const void *fn = decode_fn_for(dtype, reg_dv);
     if (!fn) return cudaErrorInvalidValue;
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-cudaError_t LPDEC_CAT(occupancy_decode_, LPDEC_D)(int dtype, int block, size_t smem, int *blocks_per_sm) {
-    const void *fn = decode_fn_for(dtype);
+cudaError_t LPDEC_CAT(occupancy_decode_, LPDEC_D)(int dtype, int reg_dv, int block, size_t smem,
+                                                   int *blocks_per_sm) {
+    const void *fn = decode_fn_for(dtype, reg_dv);
     if (!fn) return cudaErrorInvalidValue;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem);
 }
 
-cudaError_t LPDEC_CAT(launch_decode_, LPDEC_D)(int dtype, const DecodeArgs &a, const LaunchCfg &lc) {
+cudaError_t LPDEC_CAT(launch_decode_, LPDEC_D)(int dtype, int reg_dv, const DecodeArgs &a, const LaunchCfg &lc) {
     if (lc.block > kMaxT) return cudaErrorInvalidConfiguration;
-    switch (dtype) {
-        case 0: decode_kernel<kD, float, kMaxT><<<lc.grid, lc.block, lc.smem, lc.stream>>>(a); break;
-        case 1: decode_kernel<kD, __nv_bfloat16, kMaxT><<<lc.grid, lc.block, lc.smem, lc.stream>>>(a); break;
-        case 2: decode_kernel<kD, __half, kMaxT><<<lc.grid, lc.block, lc.smem, lc.stream>>>(a); break;
-        default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
+    if (kRegDV > 0 && reg_dv == kRegDV) return launch_dv<kRegDV>(dtype, a, lc);
+    return launch_dv<0>(dtype, a, lc);
 }
 
 cudaError_t LPDEC_CAT(launch_project_, LPDEC_D)(int d, long long count, const float *v, float *z,
