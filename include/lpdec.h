@@ -166,6 +166,28 @@ LPDEC_API int lpdec_decode_host(const lpdec_code *code, int32_t n_frames, const 
                       int32_t *iters_out, uint8_t *cert_out, void *cuda_stream);
 
 /*
+ * Decode one batch whose frames belong to different codes (up to 8 codes, any
+ * check degrees), in ONE persistent kernel launch: Algorithm 1 per frame with
+ * per-frame early exit (eps > 0) and the RESIDENT schedule.  A CTA decodes
+ * frames of one code at a time with that code's tile, and moves to another
+ * code when the first runs out of frames, so early-exiting frames free their
+ * slot for the next frame of any code.
+ *   codes[n_codes]:     code handles, all on the current device.
+ *   frame_code:         HOST pointer [n_frames]: the code index of each frame.
+ *   llr, x_out, bits_out: device pointers; frames packed back to back in frame
+ *                       order (frame f starts at sum_{g<f} n of code frame_code[g]).
+ *   iters_out, cert_out: device pointers [n_frames] (may be NULL), as in lpdec_decode.
+ * Results are identical to lpdec_decode of each code's frames alone.
+ * Errors: LPDEC_EINVAL for n_codes outside [1, 8], NULL arguments, a frame_code
+ * out of range, codes on different devices, the STREAMED schedule, or a code
+ * whose frame state does not fit in shared memory; plus lpdec_decode's.
+ */
+LPDEC_API int lpdec_decode_mixed(const lpdec_code *const *codes, int32_t n_codes, int32_t n_frames,
+                                 const int32_t *frame_code, const float *llr, const lpdec_params *params,
+                                 float *x_out, uint8_t *bits_out, int32_t *iters_out, uint8_t *cert_out,
+                                 void *cuda_stream);
+
+/*
  * As lpdec_decode, for callers that must not allocate device memory while they
  * run (for example a receive loop with a fixed memory footprint and a latency
  * budget that rules out allocator calls, or a host framework that owns all

@@ -279,9 +279,11 @@ int device_sm_count(int device) {
 Tile default_tile(const lpdec_code *c, int dtype) {
     Tile t;
     const int maxT = class_max_threads(c->cls);
+    const int lanes = class_lanes(kClassD[c->cls]);
+    const long long slots = (long long)c->m * lanes;  // thread slots one pass over the checks needs
     const int cap = std::min(256, maxT);
-    const int passes = (c->m + cap - 1) / cap;
-    int gt = ((c->m + passes - 1) / passes + 31) / 32 * 32;
+    const int passes = (int)((slots + cap - 1) / cap);
+    int gt = (int)(((slots + passes - 1) / passes + 31) / 32 * 32);
     gt = std::max(32, std::min(gt, cap));
     const SliceLayout L = slice_layout(c, dtype, gt);
     const int smem_cap = device_smem_optin(c->device);

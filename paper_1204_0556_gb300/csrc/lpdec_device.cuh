@@ -349,6 +349,137 @@ __device__ __forceinline__ void check_update(const CodeView &c, const IterCfg &p
     }
 }
 
+// Segmented check update: L lanes (L = 2, 4, ..., 32, aligned within the
+// warp) share one check; lane r of the segment holds entries r, r+L, r+2L, ...
+// (V = ceil(D/L) registers per lane).  The facet choice, the violation test
+// and the beta fixed point reduce over the segment with xor-shuffles.  Every
+// lane of the warp must call this with the same loop trip counts; a lane whose
+// check index is out of range passes valid = false and does no stores.
+template <int L>
+__device__ __forceinline__ float seg_sum(float x) {
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+template <int L>
+__device__ __forceinline__ int seg_sum_i(int x) {
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+template <int D, int L, typename S>
+__device__ __forceinline__ void check_update_seg(const CodeView &c, const IterCfg &p, int j, bool valid,
+                                                 S *zs, S *ls, const float *xs, bool need_res,
+                                                 float &rp, float &rd) {
+    constexpr int V = (D + L - 1) / L;
+    const int r = threadIdx.x & (L - 1);
+    int e0 = 0, d = 0;
+    if (valid) {
+        e0 = __ldg(c.row_ptr + j);
+        d = __ldg(c.row_ptr + j + 1) - e0;
+    }
+    float v[V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        const int q = k * L + r;
+        if (q < d) {
+            const int e = e0 + q;
+            const float xk = xs[__ldg(c.col_idx + e)];
+            const float zk = ld<S>(zs[e]);
+            v[k] = fmaf(p.rho, xk, p.omr * zk) + ld<S>(ls[e]);
+        } else {
+            v[k] = kPadV;
+        }
+    }
+    // facet: S = {zh > 1/2}, flip the entry closest to 1/2 when |S| is even
+    unsigned th = 0u;
+    float best = 2.0f;
+    int kb = 1 << 30;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        const float zh = __saturatef(v[k]);
+        if (zh > 0.5f) th |= 1u << k;
+        const float dist = fabsf(zh - 0.5f);
+        const int q = k * L + r;
+        if (q < d && dist < best) { best = dist; kb = q; }
+    }
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int ok = __shfl_xor_sync(0xffffffffu, kb, o);
+        if (ob < best || (ob == best && ok < kb)) { best = ob; kb = ok; }
+    }
+    const int s = seg_sum_i<L>(__popc(th));
+    if ((s & 1) == 0 && kb < d && (kb % L) == r) th ^= 1u << (kb / L);
+    const int ssz = seg_sum_i<L>(__popc(th));  // |S|, odd
+    float g = 0.0f;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        const float zh = __saturatef(v[k]);
+        g += ((th >> k) & 1u) ? zh : -zh;
+    }
+    g = seg_sum<L>(g);
+    bool done = !(d > 0 && g > (float)(ssz - 1));  // not violated: zh is the projection
+    float beta = 0.0f;
+    {
+        // fixed point of sum_k max(0, beta - kappa_k) = 1, from all entries active
+        float s1 = 0.0f;
+        int c1 = 0;
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            const int q = k * L + r;
+            if (q < d) { s1 += ((th >> k) & 1u) ? v[k] - 1.0f : -v[k]; ++c1; }
+        }
+        s1 = seg_sum<L>(s1);
+        c1 = seg_sum_i<L>(c1);
+        float cur = c1 > 0 ? __fdividef(1.0f + s1, (float)c1) : 0.0f;
+        for (int it = 0; it < D; ++it) {
+            if (__all_sync(0xffffffffu, done)) break;
+            float s2 = 0.0f;
+            int c2 = 0;
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                const int q = k * L + r;
+                const float kap = ((th >> k) & 1u) ? v[k] - 1.0f : -v[k];
+                if (q < d && kap < cur) { s2 += kap; ++c2; }
+            }
+            s2 = seg_sum<L>(s2);
+            c2 = seg_sum_i<L>(c2);
+            if (!done) {
+                const float nb = c2 > 0 ? __fdividef(1.0f + s2, (float)c2) : cur;
+                if (c2 == 0 || !(nb < cur)) {
+                    done = true;
+                    beta = fmaxf(cur, 0.0f);
+                } else {
+                    cur = nb;
+                }
+            }
+        }
+        if (!done) beta = fmaxf(cur, 0.0f);
+        if (!(d > 0 && g > (float)(ssz - 1))) beta = 0.0f;
+    }
+    Proj pr;
+    pr.facet = th;
+    pr.beta = beta;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        const int q = k * L + r;
+        if (q < d) {
+            const int e = e0 + q;
+            const float z = proj_z(v[k], pr, k);
+            if (need_res) {
+                const float a = xs[__ldg(c.col_idx + e)] - z;
+                const float b = z - ld<S>(zs[e]);
+                rp = fmaf(a, a, rp);
+                rd = fmaf(b, b, rd);
+            }
+            zs[e] = st<S>(z);
+            ls[e] = st<S>(v[k] - z);
+        }
+    }
+}
+
 // Shared-memory slice of one group: z[Ep], l[Ep] (type S), x[n] (float),
 // red[2 * nwarps] (float), flags[8] (int; the last two hold an mbarrier).
 template <typename S>
@@ -431,19 +562,30 @@ constexpr int kFrameTimeout = -2;  // iters_out value of a frame abandoned after
 // iterations (STREAMED), with one group of T threads; t is the thread's rank.
 // Every thread of the group calls this; all branches on shared data are
 // group-uniform.
+// Where one frame's inputs, outputs and (STREAMED) parked state live.
+struct FrameIO {
+    const float *llr;   // [n]
+    float *x;           // [n]
+    uint8_t *bits;      // [n] or null
+    int32_t *iters;     // one value or null
+    uint8_t *cert;      // one value or null
+    void *z_state;      // STREAMED: [Ep] of S
+    void *l_state;      // STREAMED: [Ep] of S
+    int32_t *k_state;   // STREAMED: iterations done (-1: finished); null when RESIDENT
+};
+
+// L = 1: one thread per check; L > 1: L lanes per check (segmented update).
 // Returns false only if a bulk copy timed out; the group must then stop.
-template <int D, int DV, typename S>
-__device__ bool frame_run(const DecodeArgs &a, int f, const Slice<S> &sm, int t, int T, int bar,
-                          uint32_t &phase) {
-    const CodeView &c = a.code;
-    const IterCfg &p = a.cfg;
+template <int D, int L, int DV, typename S>
+__device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, int iters_this_launch, const FrameIO &io,
+                          const Slice<S> &sm, int t, int T, int bar, uint32_t &phase) {
     const int lane = t & 31, w = t >> 5, nw = T >> 5;
     volatile int *flags = sm.flags;
-    const float *gam = a.llr + (size_t)f * c.n;
-    const bool streamed = a.k_state != nullptr;
+    const float *gam = io.llr;
+    const bool streamed = io.k_state != nullptr;
     const int state_bytes = c.Ep * (int)sizeof(S);
 
-    int k = streamed ? a.k_state[f] : 0;
+    int k = streamed ? *io.k_state : 0;
     if (k < 0) return true;  // finished in an earlier launch
     if (t == 0) { flags[0] = 0; flags[1] = 0; flags[2] = 0; }
 
@@ -457,22 +599,21 @@ __device__ bool frame_run(const DecodeArgs &a, int f, const Slice<S> &sm, int t,
         if (bad && lane == 0) atomicOr((int *)&flags[2], 1);
         group_sync(bar, T);
         if (flags[2]) {
-            float *xo = a.x_out + (size_t)f * c.n;
             for (int i = t; i < c.n; i += T) {
-                xo[i] = 0.0f;
-                if (a.bits_out) a.bits_out[(size_t)f * c.n + i] = 0;
+                io.x[i] = 0.0f;
+                if (io.bits) io.bits[i] = 0;
             }
             if (t == 0) {
-                if (a.iters_out) a.iters_out[f] = -1;
-                if (a.cert_out) a.cert_out[f] = 0;
-                if (streamed) a.k_state[f] = -1;
+                if (io.iters) *io.iters = -1;
+                if (io.cert) *io.cert = 0;
+                if (streamed) *io.k_state = -1;
             }
             return true;
         }
     } else {
         // STREAMED: bring the parked z and lambda/mu back with two bulk copies.
-        const char *zg = reinterpret_cast<const char *>(a.z_state) + (size_t)f * state_bytes;
-        const char *lg = reinterpret_cast<const char *>(a.l_state) + (size_t)f * state_bytes;
+        const void *zg = io.z_state;
+        const void *lg = io.l_state;
         if (t == 0) {
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(sm.mbar, 2u * (uint32_t)state_bytes);
@@ -484,9 +625,9 @@ __device__ bool frame_run(const DecodeArgs &a, int f, const Slice<S> &sm, int t,
         if (flags[3] == 0) {
             if (t == 0) {
                 mbar_wait_bounded(sm.mbar, phase);  // one more bounded wait for the copies in flight
-                if (a.iters_out) a.iters_out[f] = kFrameTimeout;
-                if (a.cert_out) a.cert_out[f] = 0;
-                a.k_state[f] = -1;
+                if (io.iters) *io.iters = kFrameTimeout;
+                if (io.cert) *io.cert = 0;
+                *io.k_state = -1;
             }
             return false;
         }
@@ -494,7 +635,7 @@ __device__ bool frame_run(const DecodeArgs &a, int f, const Slice<S> &sm, int t,
         phase ^= 1u;
     }
 
-    const int k_end = min(p.max_iter, k + a.iters_this_launch);
+    const int k_end = min(p.max_iter, k + iters_this_launch);
     bool conv = false, rok = false;
     while (k < k_end) {
         // ---- x-update (Algorithm 1 lines 4-6; Section 3.2)
@@ -522,7 +663,15 @@ __device__ bool frame_run(const DecodeArgs &a, int f, const Slice<S> &sm, int t,
         // ---- z- and lambda-updates (Algorithm 1 lines 7-11)
         const bool need_res = p.check_stop || (k + 1 == p.max_iter);
         float rp = 0.0f, rd = 0.0f;
-        for (int j = t; j < c.m; j += T) check_update<D, DV, S>(c, p, j, sm.z, sm.l, sm.x, need_res, rp, rd);
+        if constexpr (L == 1) {
+            for (int j = t; j < c.m; j += T) check_update<D, DV, S>(c, p, j, sm.z, sm.l, sm.x, need_res, rp, rd);
+        } else {
+            const int per_pass = T / L;
+            for (int j0 = 0; j0 < c.m; j0 += per_pass) {
+                const int j = j0 + t / L;
+                check_update_seg<D, L, S>(c, p, j, j < c.m, sm.z, sm.l, sm.x, need_res, rp, rd);
+            }
+        }
         ++k;
         if (need_res) {
             // ---- stopping test (Algorithm 1 line 13)
@@ -551,21 +700,19 @@ __device__ bool frame_run(const DecodeArgs &a, int f, const Slice<S> &sm, int t,
         // thread's shared-memory writes before them).  The next user of this
         // slice waits for the stores to finish reading it.
         if (t == 0) {
-            char *zg = reinterpret_cast<char *>(a.z_state) + (size_t)f * state_bytes;
-            char *lg = reinterpret_cast<char *>(a.l_state) + (size_t)f * state_bytes;
             fence_proxy_async_smem();
-            bulk_store(zg, sm.z, (uint32_t)state_bytes);
-            bulk_store(lg, sm.l, (uint32_t)state_bytes);
+            bulk_store(io.z_state, sm.z, (uint32_t)state_bytes);
+            bulk_store(io.l_state, sm.l, (uint32_t)state_bytes);
             bulk_commit();
-            a.k_state[f] = k;
+            *io.k_state = k;
         }
         return true;
     }
 
     // ---- outputs: x, hard decision, certificate
     float frac = 0.0f;
-    float *xo = a.x_out + (size_t)f * c.n;
-    uint8_t *bo = a.bits_out ? a.bits_out + (size_t)f * c.n : nullptr;
+    float *xo = io.x;
+    uint8_t *bo = io.bits;
     for (int i = t; i < c.n; i += T) {
         const float x = sm.x[i];
         xo[i] = x;
@@ -587,17 +734,18 @@ __device__ bool frame_run(const DecodeArgs &a, int f, const Slice<S> &sm, int t,
         float fr = 0.0f;
         bool sy = false;
         for (int q = 0; q < nw; ++q) { fr = fmaxf(fr, sm.red[2 * q]); sy |= sm.red[2 * q + 1] != 0.0f; }
-        if (a.iters_out) a.iters_out[f] = k;
-        if (a.cert_out) a.cert_out[f] = (rok && fr <= p.cert_tol && !sy) ? 1 : 0;
-        if (streamed) a.k_state[f] = -1;
+        if (io.iters) *io.iters = k;
+        if (io.cert) *io.cert = (rok && fr <= p.cert_tol && !sy) ? 1 : 0;
+        if (streamed) *io.k_state = -1;
     }
     return true;
 }
 
 // Persistent decode kernel: each group pulls frame ids from a global counter
 // until the batch is exhausted.  DV > 0 selects the regular-code form (check
-// degree D, variable degree DV).  MAXT: largest CTA size the kernel is built for.
-template <int D, int DV, typename S, int MAXT>
+// degree D, variable degree DV); L is the number of lanes per check.  MAXT:
+// largest CTA size the kernel is built for.
+template <int D, int L, int DV, typename S, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) decode_kernel(const DecodeArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int T = a.group_threads;
@@ -631,7 +779,23 @@ __global__ void __launch_bounds__(MAXT, 1) decode_kernel(const DecodeArgs a) {
         const int f = sm.flags[4 + par];
         par ^= 1;
         if (f >= a.n_frames) break;
-        if (!frame_run<D, DV, S>(a, f, sm, t, T, bar, phase)) break;
+        FrameIO io;
+        const size_t off = (size_t)f * a.code.n;
+        io.llr = a.llr + off;
+        io.x = a.x_out + off;
+        io.bits = a.bits_out ? a.bits_out + off : nullptr;
+        io.iters = a.iters_out ? a.iters_out + f : nullptr;
+        io.cert = a.cert_out ? a.cert_out + f : nullptr;
+        if (a.k_state) {
+            const size_t sb = (size_t)a.code.Ep * sizeof(S);
+            io.z_state = reinterpret_cast<char *>(a.z_state) + (size_t)f * sb;
+            io.l_state = reinterpret_cast<char *>(a.l_state) + (size_t)f * sb;
+            io.k_state = a.k_state + f;
+        } else {
+            io.z_state = io.l_state = nullptr;
+            io.k_state = nullptr;
+        }
+        if (!frame_run<D, L, DV, S>(a.code, a.cfg, a.iters_this_launch, io, sm, t, T, bar, phase)) break;
     }
     if (t == 0) bulk_wait_all();
 }
@@ -650,5 +814,45 @@ __global__ void __launch_bounds__(256) project_kernel(int d, long long count, co
     for (int k = 0; k < D; ++k)
         if (k < d) z[i * d + k] = proj_z(vv[k], pr, k);
 }
+
+}  // namespace lpdec
+
+namespace lpdec {
+
+// ---------------------------------------------------------------------------
+// Mixed-code batches: one persistent launch decodes frames of several codes.
+constexpr int kMaxMixedCodes = 8;
+// CTA size bound of the mixed kernel: holding every kernel form in one
+// function needs more than the 64 registers a 1024-thread CTA leaves.
+constexpr int kMixedMaxThreads = 768;
+
+// Kernel forms a code can run in (check degree class D, lanes per check L,
+// regular variable degree DV or 0).
+enum MixedKind : int { kK6R3 = 0, kK6 = 1, kK8R4 = 2, kK8 = 3, kK16 = 4, kK20 = 5, kK32 = 6, kNumKinds = 7 };
+
+struct MixedCode {
+    CodeView view;
+    IterCfg cfg;         // per code: the stopping constants scale with its E
+    int kind;            // MixedKind
+    int groups;          // frames decoded at once by a CTA working on this code
+    int group_threads;   // threads per frame
+    int smem_per_group;  // bytes of one slice
+    int off_x, off_red;  // slice layout
+    int n_frames;        // frames of this code in the batch
+    const int *frames;   // [n_frames] their frame ids
+};
+
+struct MixedArgs {
+    int n_codes;
+    MixedCode code[kMaxMixedCodes];
+    int home_end[kMaxMixedCodes];  // CTA b starts on the first code c with b < home_end[c]
+    const long long *offset;       // [F] element offset of frame f in llr, x_out and bits_out
+    const float *llr;
+    float *x_out;
+    uint8_t *bits_out;
+    int32_t *iters_out;
+    uint8_t *cert_out;
+    int *queues;                   // [n_codes] work-queue counters, zero at launch
+};
 
 }  // namespace lpdec

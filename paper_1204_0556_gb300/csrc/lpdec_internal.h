@@ -20,8 +20,13 @@ inline int degree_class(int max_dc) {
     return -1;
 }
 
-// Largest CTA the decode kernel of a class is compiled for (register budget).
-inline int class_max_threads(int cls) { return kClassD[cls] <= 8 ? 1024 : 512; }
+// Lanes per check in the decode kernel of a class: one thread per check for
+// D <= 8 (sorted breakpoints), a segment of lanes for wider checks so that
+// each lane holds at most 8 entries.
+constexpr int class_lanes(int D) { return D <= 8 ? 1 : (D <= 16 ? 2 : 4); }
+
+// Largest CTA the decode kernel of a class is compiled for.
+inline int class_max_threads(int cls) { return 1024; }
 
 struct LaunchCfg {
     int grid;

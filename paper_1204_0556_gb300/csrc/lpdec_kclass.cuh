@@ -14,13 +14,14 @@ namespace lpdec {
 
 namespace {
 constexpr int kD = LPDEC_D;
-constexpr int kMaxT = kD <= 8 ? 1024 : 512;
+constexpr int kL = class_lanes(kD);
+constexpr int kMaxT = 1024;
 // Variable degree of the regular-code kernel built for this class (0: none).
 constexpr int kRegDV = kD == 6 ? 3 : (kD == 8 ? 4 : 0);
 
 template <int DV, typename S>
 const void *decode_fn() {
-    return reinterpret_cast<const void *>(&decode_kernel<kD, DV, S, kMaxT>);
+    return reinterpret_cast<const void *>(&decode_kernel<kD, kL, DV, S, kMaxT>);
 }
 
 template <int DV>
@@ -41,9 +42,9 @@ const void *decode_fn_for(int dtype, int reg_dv) {
 template <int DV>
 cudaError_t launch_dv(int dtype, const DecodeArgs &a, const LaunchCfg &lc) {
     switch (dtype) {
-        case 0: decode_kernel<kD, DV, float, kMaxT><<<lc.grid, lc.block, lc.smem, lc.stream>>>(a); break;
-        case 1: decode_kernel<kD, DV, __nv_bfloat16, kMaxT><<<lc.grid, lc.block, lc.smem, lc.stream>>>(a); break;
-        case 2: decode_kernel<kD, DV, __half, kMaxT><<<lc.grid, lc.block, lc.smem, lc.stream>>>(a); break;
+        case 0: decode_kernel<kD, kL, DV, float, kMaxT><<<lc.grid, lc.block, lc.smem, lc.stream>>>(a); break;
+        case 1: decode_kernel<kD, kL, DV, __nv_bfloat16, kMaxT><<<lc.grid, lc.block, lc.smem, lc.stream>>>(a); break;
+        case 2: decode_kernel<kD, kL, DV, __half, kMaxT><<<lc.grid, lc.block, lc.smem, lc.stream>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

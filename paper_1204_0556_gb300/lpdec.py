@@ -37,6 +37,7 @@ EXPORTED = [
     "lpdec_params_default", "lpdec_last_error", "lpdec_version",
     "lpdec_code_create", "lpdec_code_info", "lpdec_code_destroy",
     "lpdec_decode", "lpdec_decode_host", "lpdec_project", "lpdec_decode_noalloc",
+    "lpdec_decode_mixed",
 ]
 
 
@@ -90,6 +91,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
             "lpdec_decode_host": (ctypes.c_int, [_vp, _i32, _vp, P, _vp, _vp, _vp, _vp, _vp]),
             "lpdec_project": (ctypes.c_int, [_i32, _i64, _vp, _vp, _vp]),
             "lpdec_decode_noalloc": (ctypes.c_int, [_vp, _i32, _vp, P, _vp, _vp, _vp, _vp, _vp]),
+            "lpdec_decode_mixed": (ctypes.c_int, [ctypes.POINTER(_vp), _i32, _i32, _i32p, _vp, P, _vp, _vp, _vp,
+                                                  _vp, _vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -159,6 +162,14 @@ def lpdec_decode_noalloc(handle, n_frames, llr_ptr, params, x_ptr, bits_ptr, ite
     during the call (for callers that cannot allocate device memory as they run)."""
     _check(load().lpdec_decode_noalloc(handle, n_frames, llr_ptr, ctypes.byref(params), x_ptr, bits_ptr,
                                        iters_ptr, cert_ptr, stream_ptr))
+
+
+def lpdec_decode_mixed(handles, n_frames, frame_code, llr_ptr, params, x_ptr, bits_ptr, iters_ptr, cert_ptr,
+                       stream_ptr) -> None:
+    arr = (_vp * len(handles))(*handles)
+    fc = _i32arr(frame_code)
+    _check(load().lpdec_decode_mixed(arr, len(handles), n_frames, fc.ctypes.data_as(_i32p), llr_ptr,
+                                     ctypes.byref(params), x_ptr, bits_ptr, iters_ptr, cert_ptr, stream_ptr))
 
 
 def lpdec_project(d, count, v_ptr, z_ptr, stream_ptr) -> None:
@@ -240,6 +251,30 @@ def decode_host(code: Code, llr: np.ndarray, params: lpdec_params | None = None,
                "iters": np.empty(F, np.int32), "cert": np.empty(F, np.uint8)}
     lpdec_decode_host(code.handle, F, llr.ctypes.data, params, out["x"].ctypes.data, out["bits"].ctypes.data,
                       out["iters"].ctypes.data, out["cert"].ctypes.data, _stream_ptr(stream))
+    return out
+
+
+def decode_mixed(codes: list, frame_code, llr, params: lpdec_params | None = None, stream=None,
+                 out: dict | None = None) -> dict:
+    """Decode a packed batch of frames of several codes in one persistent launch.
+
+    ``llr`` is a 1-D float32 CUDA tensor with the frames back to back in frame
+    order; ``frame_code`` (host ints) gives each frame's index into ``codes``."""
+    import torch
+
+    fc = np.ascontiguousarray(frame_code, dtype=np.int32)
+    F = len(fc)
+    total = int(sum(codes[c].n for c in fc))
+    if not (llr.is_cuda and llr.dtype == torch.float32 and llr.is_contiguous() and llr.numel() == total):
+        raise ValueError("llr must be a contiguous float32 CUDA tensor of sum(n) elements")
+    params = params or make_params()
+    if out is None:
+        out = {"x": torch.empty(total, dtype=torch.float32, device=llr.device),
+               "bits": torch.empty(total, dtype=torch.uint8, device=llr.device),
+               "iters": torch.empty(F, dtype=torch.int32, device=llr.device),
+               "cert": torch.empty(F, dtype=torch.uint8, device=llr.device)}
+    lpdec_decode_mixed([c.handle for c in codes], F, fc, llr.data_ptr(), params, out["x"].data_ptr(),
+                       out["bits"].data_ptr(), out["iters"].data_ptr(), out["cert"].data_ptr(), _stream_ptr(stream))
     return out
 
 
