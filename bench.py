@@ -49,6 +49,14 @@ def parse():
     ap.add_argument("--variants", type=int, default=1, help="also time the other schedules/precisions")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="single", choices=["single", "mixed", "precision", "served"],
+                    help="single: the headline C1056 batch; mixed: three codes in one persistent launch; "
+                         "precision: FP32 / BF16 / FP16 state storage; served: Poisson request stream")
+    ap.add_argument("--served-rate", type=float, default=2e5, help="offered load, frames/s")
+    ap.add_argument("--served-requests", type=int, default=200_000)
+    ap.add_argument("--served-round", type=int, default=8, help="ADMM iterations per server round")
+    ap.add_argument("--mixed-frames", type=int, default=30_000)
+    ap.add_argument("--precision-frames", type=int, default=100_000)
     return ap.parse_args()
 
 
@@ -189,11 +197,235 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def _time_call(fn, steps, warmup):
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_mixed(args):
+    """Three codes interleaved 40/40/20 in one persistent launch, per-frame early exit."""
+    import torch
+
+    from paper_1204_0556_gb300 import build, inputs as I, lpdec
+
+    build.build()
+    codes = [I.benchmark_code("C1056", 0), I.benchmark_code("C2640", 1), I.benchmark_code("C4000", 2)]
+    F = args.mixed_frames
+    counts = [int(0.4 * F), int(0.4 * F), F - 2 * int(0.4 * F)]
+    order = np.random.Generator(np.random.Philox(key=3)).permutation(F)
+    fc = np.concatenate([np.full(n, c, dtype=np.int32) for c, n in enumerate(counts)])[order]
+    snr = np.random.Generator(np.random.Philox(key=4)).uniform(1.5, 4.0, F)
+    per_code = {}
+    for c, code in enumerate(codes):
+        idx = np.nonzero(fc == c)[0]
+        per_code[c] = (idx, I.awgn_llr(code, snr[idx], len(idx), 40 + c))
+    offsets = np.concatenate([[0], np.cumsum([codes[c].n for c in fc])])
+    packed = np.empty(offsets[-1], dtype=np.float32)
+    for c, (idx, llr) in per_code.items():
+        for r, f in enumerate(idx):
+            packed[offsets[f]:offsets[f + 1]] = llr[r]
+    Cs = [lpdec.Code(cd) for cd in codes]
+    p = lpdec.make_params(mu=MU, rho=RHO, eps=1e-5, max_iter=1000, state="f32", schedule="resident")
+    d_packed = torch.from_numpy(packed).cuda()
+    out = lpdec.decode_mixed(Cs, fc, d_packed, p)
+    ms_mixed = _time_call(lambda: lpdec.decode_mixed(Cs, fc, d_packed, p, out=out), args.steps, args.warmup)
+    iters = out["iters"].cpu().numpy()
+    bits = out["bits"].cpu().numpy()
+    word_err = np.array([bits[offsets[f]:offsets[f + 1]].any() for f in range(F)])
+    info = sum(codes[c].k_design for c in fc)
+    # the same frames as plain single-code launches (frames grouped per code)
+    d_per = {c: torch.from_numpy(llr).cuda() for c, (idx, llr) in per_code.items()}
+    outs = {c: lpdec.decode(Cs[c], d_per[c], p) for c in d_per}
+
+    def per_code_resident():
+        for c in d_per:
+            lpdec.decode(Cs[c], d_per[c], p, out=outs[c])
+
+    ps = lpdec.make_params(mu=MU, rho=RHO, eps=1e-5, max_iter=1000, state="f32", schedule="streamed")
+
+    def per_code_streamed():
+        for c in d_per:
+            lpdec.decode(Cs[c], d_per[c], ps, out=outs[c])
+
+    ms_res = _time_call(per_code_resident, max(1, args.steps), 1)
+    ms_str = _time_call(per_code_streamed, 1, 1)
+    line = {
+        "workload": "mixed", "metric": "ADMM-LP decoded info bits/s, mixed-code batch", "unit": UNIT,
+        "value": info / (ms_mixed / 1000.0), "ms_per_step": ms_mixed, "steps": args.steps, "warmup": args.warmup,
+        "frames": F, "frames_per_s": F / (ms_mixed / 1000.0),
+        "config": {"codes": "C1056 (3,6) seed 0, C2640 (4,8) seed 1, C4000 (3,30) m=400 seed 2",
+                   "mix": f"{counts[0]}/{counts[1]}/{counts[2]} interleaved by a seeded shuffle",
+                   "snr": "Eb/N0 uniform in [1.5, 4.0] dB per frame", "eps": 1e-5, "max_iter": 1000,
+                   "dtype": "f32", "launches_per_step": 1},
+        "mean_iters": {codes[c].name: float(iters[fc == c].mean()) for c in range(3)},
+        "wer": {codes[c].name: float(word_err[fc == c].mean()) for c in range(3)},
+        "vs_plain": {
+            "per_code_resident_launches": {"value": info / (ms_res / 1000.0), "ms_per_step": ms_res,
+                                           "launches_per_step": 3},
+            "per_code_streamed_launches": {"value": info / (ms_str / 1000.0), "ms_per_step": ms_str,
+                                           "launches_per_step": 3000},
+        },
+    }
+    for C in Cs:
+        C.close()
+    print(json.dumps(line), flush=True)
+
+
+def run_precision(args):
+    """FP32 vs BF16 vs FP16 z/lambda storage (FP32 arithmetic), fixed 300 iterations."""
+    import torch
+
+    import oracle
+    from paper_1204_0556_gb300 import build, inputs as I, lpdec
+
+    build.build()
+    oracle.build()
+    F = args.precision_frames
+    rows = []
+    for name, hseed in (("C1056", 0), ("C4000", 2)):
+        code = I.benchmark_code(name, hseed)
+        C = lpdec.Code(code)
+        for pt, snr in enumerate((2.5, 4.0)):
+            llr = I.awgn_llr(code, snr, F, 200 + pt)
+            d_llr = torch.from_numpy(llr).cuda()
+            sample = np.linspace(0, F - 1, 48).astype(int)
+            ref = oracle.decode(code.row_ptr, code.col_idx, code.n, llr[sample].astype(np.float64), mu=MU, rho=RHO,
+                                eps=0.0, max_iter=ITERS)
+            for state in ("f32", "bf16", "f16"):
+                for sched in ("resident", "streamed"):
+                    p = lpdec.make_params(mu=MU, rho=RHO, eps=0.0, max_iter=ITERS, state=state, schedule=sched)
+                    out = lpdec.decode(C, d_llr, p)
+                    ms = _time_call(lambda: lpdec.decode(C, d_llr, p, out=out), max(1, args.steps // 2), 1)
+                    x = out["x"].cpu().numpy()
+                    bits = out["bits"].cpu().numpy()
+                    rows.append({
+                        "code": name, "snr_db": snr, "state": state, "schedule": sched,
+                        "value": F * code.k_design / (ms / 1000.0), "ms_per_step": ms,
+                        "hbm_frac": round(F * ITERS * algorithmic_bytes_per_frame_iter(code, 4 if state == "f32"
+                                                                                        else 2)
+                                          / (ms / 1000.0) / 1e9 / measured_peaks()[0], 4),
+                        "wer": float(bits.any(axis=1).mean()),
+                        "max_abs_x_err_vs_oracle": float(np.abs(x[sample] - ref["x"]).max()),
+                    })
+        C.close()
+    print(json.dumps({"workload": "precision", "frames_per_point": F, "iters": ITERS, "unit": UNIT,
+                      "oracle_sample": "48 evenly spaced frames per point", "rows": rows}), flush=True)
+
+
+def run_served(args):
+    """Poisson arrivals of one-frame requests over four codes into lpdec_server."""
+    import torch
+
+    from paper_1204_0556_gb300 import build, inputs as I, lpdec
+
+    build.build()
+    names = ["C96", "C1056", "C2640", "C8000"]
+    codes = [I.benchmark_code(nm, k) for k, nm in enumerate(names)]
+    handles = [lpdec.Code(c) for c in codes]
+    R = args.served_requests
+    arrivals = np.cumsum(np.random.Generator(np.random.Philox(key=5)).exponential(1.0 / args.served_rate, R))
+    which = np.random.Generator(np.random.Philox(key=6)).integers(0, 4, R).astype(np.int32)
+    snr_rng = np.random.Generator(np.random.Philox(key=7))
+    # A pool of 2048 seeded frames per code (Eb/N0 uniform in [1.5, 4.5] dB each)
+    # is cycled through; a request's frame is drawn once per request.
+    POOL = 2048
+    pools = [I.awgn_llr(c, snr_rng.uniform(1.5, 4.5, POOL), POOL, 8 + 10 * k) for k, c in enumerate(codes)]
+    p = lpdec.make_params(mu=MU, rho=RHO, eps=1e-5, max_iter=1000, state="f32", iters_per_launch=args.served_round)
+    srv = lpdec.Server(budget_bytes=8 << 30)
+    ids = [srv.add_code(h) for h in handles]
+    ptrs = [[pl[i].ctypes.data for i in range(POOL)] for pl in pools]
+    outx = [np.empty(c.n, np.float32) for c in codes]
+    outb = [np.empty(c.n, np.uint8) for c in codes]
+    it_buf, ce_buf = np.empty(1, np.int32), np.empty(1, np.uint8)
+    rid = np.zeros(R, dtype=np.uint64)
+    iters = np.zeros(R, dtype=np.int32)
+    err = np.zeros(R, dtype=bool)
+    submit_lag = np.zeros(R)
+    cursor = [0, 0, 0, 0]
+    sub_fn = lpdec.load().lpdec_server_submit
+    poll_fn = lpdec.load().lpdec_server_poll
+    import ctypes
+
+    rid_c = ctypes.c_uint64()
+    done_submit = threading.Event()
+    submitted = [0]
+
+    def poller():
+        for i in range(R):
+            while submitted[0] <= i:
+                time.sleep(0.0002)
+            c = which[i]
+            st = poll_fn(srv.handle, int(rid[i]), -1, outx[c].ctypes.data, outb[c].ctypes.data, it_buf.ctypes.data,
+                         ce_buf.ctypes.data)
+            if st != 0:
+                raise RuntimeError(lpdec.lpdec_last_error())
+            iters[i] = it_buf[0]
+            err[i] = bool(outb[c].any())
+
+    th = threading.Thread(target=poller)
+    th.start()
+    t0 = time.perf_counter()
+    for i in range(R):
+        while time.perf_counter() - t0 < arrivals[i]:
+            pass
+        c = which[i]
+        k = cursor[c]
+        cursor[c] = (k + 1) % POOL
+        st = sub_fn(srv.handle, ids[c], 1, ptrs[c][k], ctypes.byref(p), ctypes.byref(rid_c))
+        if st != 0:
+            raise RuntimeError(lpdec.lpdec_last_error())
+        rid[i] = rid_c.value
+        submit_lag[i] = (time.perf_counter() - t0) - arrivals[i]
+        submitted[0] = i + 1
+    done_submit.set()
+    th.join()
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    for h in handles:
+        h.close()
+    info = sum(codes[c].k_design for c in which)
+    line = {
+        "workload": "served", "metric": "ADMM-LP served decode stream: sustained info bits/s, p50/p99 latency",
+        "unit": UNIT, "value": st["bits_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+        "frames": int(st["frames"]), "wall_s": wall, "info_bits_per_s_wall": info / wall,
+        "offered_frames_per_s": args.served_rate, "achieved_submit_frames_per_s": R / (arrivals[-1] + submit_lag[-1]),
+        "submit_lag_ms_p99": float(np.quantile(submit_lag, 0.99) * 1000),
+        "config": {"codes": "C96, C1056, C2640, C8000 (irregular dc 6..20, dv 3), uniform per request",
+                   "snr": "Eb/N0 uniform in [1.5, 4.5] dB", "eps": 1e-5, "max_iter": 1000,
+                   "iters_per_round": args.served_round, "budget_bytes": 8 << 30,
+                   "arrivals": f"Poisson, {args.served_rate:.0f} frames/s, {R} one-frame requests",
+                   "frames": "2048 seeded frames per code, cycled"},
+        "mean_iters": {names[c]: float(iters[which == c].mean()) for c in range(4)},
+        "wer": {names[c]: float(err[which == c].mean()) for c in range(4)},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.workload == "mixed":
+        run_mixed(args)
+        return
+    if args.workload == "precision":
+        run_precision(args)
+        return
+    if args.workload == "served":
+        run_served(args)
         return
 
     import torch

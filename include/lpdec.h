@@ -210,6 +210,58 @@ LPDEC_API int lpdec_decode_noalloc(const lpdec_code *code, int32_t n_frames, con
                                    const lpdec_params *params, float *x_out, uint8_t *bits_out,
                                    int32_t *iters_out, uint8_t *cert_out, void *cuda_stream);
 
+/* ---- serving ----------------------------------------------------------- */
+
+/*
+ * A continuous-batching decode server on the current device.  Each code added
+ * gets a pool of frame slots in device memory (LLRs, outputs and the z/lambda
+ * state of frames in flight).  A scheduler thread, started by the first
+ * submit, repeats rounds: admit queued frames into free slots, advance every
+ * frame in flight by params.iters_per_launch ADMM iterations in one launch per
+ * code, and retire frames that converged or reached max_iter (Algorithm 1 per
+ * frame, early exit by the stopping test).  Requests that arrive while others
+ * are on the GPU join the next round.  A frame's result is identical to
+ * lpdec_decode of that frame alone.
+ *   device_budget_bytes: upper bound on the device memory of all slot pools.
+ *   cuda_stream: stream for the server's work, or NULL for a private stream.
+ */
+LPDEC_API int lpdec_server_create(size_t device_budget_bytes, void *cuda_stream, lpdec_server **out);
+
+/* Register a code; *code_id indexes it in later submits.  The code must
+ * outlive the server. */
+LPDEC_API int lpdec_server_add_code(lpdec_server *server, const lpdec_code *code, int32_t *code_id);
+
+/*
+ * Queue a request of n_frames frames of one code.  llr_host: HOST pointer
+ * [n_frames x n], copied before the call returns.  The first request of a code
+ * fixes that code's parameters and sizes its slot pool (min(4096, what is left
+ * of the budget) slots); later requests of the code must pass the same
+ * parameters.  Errors: LPDEC_EINVAL (bad arguments, different parameters),
+ * LPDEC_ENOMEM (budget exhausted), LPDEC_EBUSY (too many frames queued),
+ * LPDEC_ECLOSED (server shutting down), or the status of a failed scheduler.
+ */
+LPDEC_API int lpdec_server_submit(lpdec_server *server, int32_t code_id, int32_t n_frames, const float *llr_host,
+                                  const lpdec_params *params, uint64_t *request_id);
+
+/*
+ * Wait up to timeout_ms (< 0: no limit) for a request; when done, copy its
+ * outputs to the HOST buffers (any may be NULL; shapes as in lpdec_decode) and
+ * release it (a request can be polled to completion once).  LPDEC_ETIMEOUT if
+ * not done in time (the request stays queued); LPDEC_EINVAL for an unknown id.
+ */
+LPDEC_API int lpdec_server_poll(lpdec_server *server, uint64_t request_id, int32_t timeout_ms, float *x,
+                                uint8_t *bits, int32_t *iters, uint8_t *cert);
+
+/* Latency percentiles of completed requests (submit to completion, host clock),
+ * decoded information bits per second since the first submit (design rate
+ * k = n - m per frame), and frames completed.  Any pointer may be NULL. */
+LPDEC_API int lpdec_server_stats(lpdec_server *server, double *p50_ms, double *p99_ms, double *bits_per_s,
+                                 int64_t *frames);
+
+/* Stop accepting requests, finish the frames already submitted, free the
+ * server.  Calls racing with destroy on other threads get LPDEC_ECLOSED. */
+LPDEC_API int lpdec_server_destroy(lpdec_server *server);
+
 /*
  * Euclidean projection onto the parity polytope PP_d (Section 4.4, Algorithm 2)
  * of `count` vectors of dimension d, 1 <= d <= 32, computed exactly as the

@@ -428,6 +428,22 @@ int enqueue_decode(const lpdec_code *c, int n_frames, const float *llr, const lp
     return LPDEC_OK;
 }
 
+// Plan and launch the decode kernel once with caller-filled arguments (frame
+// buffers, state, queue, frame list); fills the tile fields of `a`.
+int launch_once(const lpdec_code *c, int dtype, const Tile &tile, DecodeArgs &a, cudaStream_t stream) {
+    LaunchCfg lc;
+    SliceLayout L;
+    int rc = plan_launch(c, dtype, tile, a.n_frames, stream, &lc, &L);
+    if (rc) return rc;
+    a.group_threads = tile.group_threads;
+    a.smem_per_group = (int)L.bytes;
+    a.off_x = (int)L.off_x;
+    a.off_red = (int)L.off_red;
+    cudaError_t err = class_launch(c, dtype, a, lc);
+    if (err != cudaSuccess) return cuda_error(err, "decode kernel launch");
+    return LPDEC_OK;
+}
+
 }  // namespace lpdec
 
 // ---------------------------------------------------------------------------

@@ -35,6 +35,7 @@ int plan_launch(const lpdec_code *c, int dtype, const Tile &tile, int n_frames, 
                 LaunchCfg *lc, SliceLayout *layout);
 int resolve_schedule(const lpdec_code *c, const lpdec_params *p, const Tile &tile);
 size_t workspace_bytes(const lpdec_code *c, int n_frames, int schedule, int dtype, int max_iter, int ipl);
+int launch_once(const lpdec_code *c, int dtype, const Tile &tile, DecodeArgs &a, cudaStream_t stream);
 int enqueue_decode(const lpdec_code *c, int n_frames, const float *llr, const lpdec_params *p, float *x_out,
                    uint8_t *bits_out, int32_t *iters_out, uint8_t *cert_out, cudaStream_t stream, void *work,
                    int schedule, const Tile &tile, int *launches_out);

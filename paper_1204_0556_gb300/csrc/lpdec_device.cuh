@@ -241,6 +241,7 @@ struct DecodeArgs {
     void *l_state;           // [F x Ep] of S (lambda/mu)
     int32_t *k_state;        // [F] iterations done; -1 once the frame is finished
     int iters_this_launch;   // RESIDENT: max_iter
+    const int *frame_list;   // [n_frames] ids of the frames to run, or null for 0..n_frames-1
     int *queue;              // frame work-queue counter, zero at launch
     int group_threads;       // GT, a multiple of 32
     int smem_per_group;      // bytes of one group's slice
@@ -776,9 +777,10 @@ __global__ void __launch_bounds__(MAXT, 1) decode_kernel(const DecodeArgs a) {
             sm.flags[4 + par] = atomicAdd(a.queue, 1);
         }
         group_sync(bar, T);
-        const int f = sm.flags[4 + par];
+        const int q = sm.flags[4 + par];
         par ^= 1;
-        if (f >= a.n_frames) break;
+        if (q >= a.n_frames) break;
+        const int f = a.frame_list ? a.frame_list[q] : q;
         FrameIO io;
         const size_t off = (size_t)f * a.code.n;
         io.llr = a.llr + off;

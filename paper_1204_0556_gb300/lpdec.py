@@ -38,6 +38,8 @@ EXPORTED = [
     "lpdec_code_create", "lpdec_code_info", "lpdec_code_destroy",
     "lpdec_decode", "lpdec_decode_host", "lpdec_project", "lpdec_decode_noalloc",
     "lpdec_decode_mixed",
+    "lpdec_server_create", "lpdec_server_add_code", "lpdec_server_submit", "lpdec_server_poll",
+    "lpdec_server_stats", "lpdec_server_destroy",
 ]
 
 
@@ -94,6 +96,16 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
             "lpdec_decode_mixed": (ctypes.c_int, [ctypes.POINTER(_vp), _i32, _i32, _i32p, _vp, P, _vp, _vp, _vp,
                                                   _vp, _vp]),
         }
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        dp = ctypes.POINTER(ctypes.c_double)
+        sig.update({
+            "lpdec_server_create": (ctypes.c_int, [ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]),
+            "lpdec_server_add_code": (ctypes.c_int, [_vp, _vp, _i32p]),
+            "lpdec_server_submit": (ctypes.c_int, [_vp, _i32, _i32, _vp, P, u64p]),
+            "lpdec_server_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, _i32, _vp, _vp, _vp, _vp]),
+            "lpdec_server_stats": (ctypes.c_int, [_vp, dp, dp, dp, ctypes.POINTER(_i64)]),
+            "lpdec_server_destroy": (ctypes.c_int, [_vp]),
+        })
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
             fn.restype = res
@@ -170,6 +182,44 @@ def lpdec_decode_mixed(handles, n_frames, frame_code, llr_ptr, params, x_ptr, bi
     fc = _i32arr(frame_code)
     _check(load().lpdec_decode_mixed(arr, len(handles), n_frames, fc.ctypes.data_as(_i32p), llr_ptr,
                                      ctypes.byref(params), x_ptr, bits_ptr, iters_ptr, cert_ptr, stream_ptr))
+
+
+def lpdec_server_create(budget_bytes: int, stream_ptr: int = 0) -> int:
+    out = _vp()
+    _check(load().lpdec_server_create(budget_bytes, stream_ptr, ctypes.byref(out)))
+    return out.value
+
+
+def lpdec_server_add_code(server: int, code_handle: int) -> int:
+    cid = _i32()
+    _check(load().lpdec_server_add_code(server, code_handle, ctypes.byref(cid)))
+    return cid.value
+
+
+def lpdec_server_submit(server: int, code_id: int, n_frames: int, llr_ptr: int, params) -> int:
+    rid = ctypes.c_uint64()
+    _check(load().lpdec_server_submit(server, code_id, n_frames, llr_ptr, ctypes.byref(params), ctypes.byref(rid)))
+    return rid.value
+
+
+def lpdec_server_poll(server: int, request_id: int, timeout_ms: int, x_ptr, bits_ptr, iters_ptr, cert_ptr) -> int:
+    """Returns the status (LPDEC_OK or LPDEC_ETIMEOUT); other errors raise."""
+    st = load().lpdec_server_poll(server, request_id, timeout_ms, x_ptr, bits_ptr, iters_ptr, cert_ptr)
+    if st not in (LPDEC_OK, LPDEC_ETIMEOUT):
+        _check(st)
+    return st
+
+
+def lpdec_server_stats(server: int) -> dict:
+    p50, p99, bps = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    fr = _i64()
+    _check(load().lpdec_server_stats(server, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(bps),
+                                     ctypes.byref(fr)))
+    return {"p50_ms": p50.value, "p99_ms": p99.value, "bits_per_s": bps.value, "frames": fr.value}
+
+
+def lpdec_server_destroy(server: int) -> None:
+    _check(load().lpdec_server_destroy(server))
 
 
 def lpdec_project(d, count, v_ptr, z_ptr, stream_ptr) -> None:
@@ -276,6 +326,38 @@ def decode_mixed(codes: list, frame_code, llr, params: lpdec_params | None = Non
     lpdec_decode_mixed([c.handle for c in codes], F, fc, llr.data_ptr(), params, out["x"].data_ptr(),
                        out["bits"].data_ptr(), out["iters"].data_ptr(), out["cert"].data_ptr(), _stream_ptr(stream))
     return out
+
+
+class Server:
+    """Continuous-batching decode server (thin wrapper over lpdec_server_*)."""
+
+    def __init__(self, budget_bytes: int = 8 << 30, stream=None):
+        self.handle = lpdec_server_create(budget_bytes, 0 if stream is None else int(stream.cuda_stream))
+        self.codes = []
+
+    def add_code(self, code: Code) -> int:
+        self.codes.append(code)
+        return lpdec_server_add_code(self.handle, code.handle)
+
+    def submit(self, code_id: int, llr: np.ndarray, params: lpdec_params) -> int:
+        llr = np.ascontiguousarray(np.atleast_2d(llr), dtype=np.float32)
+        return lpdec_server_submit(self.handle, code_id, llr.shape[0], llr.ctypes.data, params)
+
+    def poll(self, request_id: int, code_id: int, n_frames: int = 1, timeout_ms: int = -1):
+        n = self.codes[code_id].n
+        out = {"x": np.empty((n_frames, n), np.float32), "bits": np.empty((n_frames, n), np.uint8),
+               "iters": np.empty(n_frames, np.int32), "cert": np.empty(n_frames, np.uint8)}
+        st = lpdec_server_poll(self.handle, request_id, timeout_ms, out["x"].ctypes.data, out["bits"].ctypes.data,
+                               out["iters"].ctypes.data, out["cert"].ctypes.data)
+        return out if st == LPDEC_OK else None
+
+    def stats(self) -> dict:
+        return lpdec_server_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            lpdec_server_destroy(self.handle)
+            self.handle = None
 
 
 def project(v, stream=None):

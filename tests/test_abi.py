@@ -97,12 +97,23 @@ def test_decode_and_project_reject_bad_arguments(lib):
 
 
 def test_python_binding_fails_loudly_without_library(tmp_path):
-    import importlib
-
-    mod = importlib.reload(L)
+    saved = L._lib
     try:
-        mod._lib = None
+        L._lib = None
         with pytest.raises(RuntimeError, match="not found"):
-            mod.load(str(tmp_path / "missing.so"))
+            L.load(str(tmp_path / "missing.so"))
     finally:
-        mod._lib = None
+        L._lib = saved
+
+
+def test_server_entry_points_reject_null_arguments(lib):
+    rid = ctypes.c_uint64()
+    p = L.lpdec_params_default()
+    assert lib.lpdec_server_create(1 << 20, None, None) == L.LPDEC_EINVAL
+    assert lib.lpdec_server_add_code(None, None, None) == L.LPDEC_EINVAL
+    assert lib.lpdec_server_submit(None, 0, 1, None, ctypes.byref(p), ctypes.byref(rid)) == L.LPDEC_EINVAL
+    assert lib.lpdec_server_poll(None, 1, 0, None, None, None, None) == L.LPDEC_EINVAL
+    assert lib.lpdec_server_stats(None, None, None, None, None) == L.LPDEC_EINVAL
+    assert lib.lpdec_server_destroy(None) == L.LPDEC_EINVAL
+    assert lib.lpdec_decode_mixed(None, 0, 0, None, None, ctypes.byref(p), None, None, None, None, None) \
+        == L.LPDEC_EINVAL
