@@ -212,6 +212,19 @@ def _time_call(fn, steps, warmup):
     return e0.elapsed_time(e1) / steps
 
 
+def autotune_codes(lpdec, handles, llrs, state):
+    """Pick each code's tile with lpdec_autotune on up to 2048 of its frames (60 fixed iterations)."""
+    import torch
+
+    tiles = []
+    for C, llr in zip(handles, llrs):
+        sample = torch.from_numpy(np.ascontiguousarray(llr[:2048])).cuda()
+        p = lpdec.make_params(mu=MU, rho=RHO, eps=0.0, max_iter=60, state=state, schedule="resident")
+        tiles.append(lpdec.lpdec_autotune(C.handle, p, sample.shape[0], sample.data_ptr(),
+                                          int(torch.cuda.current_stream().cuda_stream)))
+    return tiles
+
+
 def run_mixed(args):
     """Three codes interleaved 40/40/20 in one persistent launch, per-frame early exit."""
     import torch
@@ -236,6 +249,7 @@ def run_mixed(args):
             packed[offsets[f]:offsets[f + 1]] = llr[r]
     Cs = [lpdec.Code(cd) for cd in codes]
     p = lpdec.make_params(mu=MU, rho=RHO, eps=1e-5, max_iter=1000, state="f32", schedule="resident")
+    tiles = autotune_codes(lpdec, Cs, [per_code[c][1] for c in range(3)], "f32")
     d_packed = torch.from_numpy(packed).cuda()
     out = lpdec.decode_mixed(Cs, fc, d_packed, p)
     ms_mixed = _time_call(lambda: lpdec.decode_mixed(Cs, fc, d_packed, p, out=out), args.steps, args.warmup)
@@ -269,6 +283,7 @@ def run_mixed(args):
                    "dtype": "f32", "launches_per_step": 1},
         "mean_iters": {codes[c].name: float(iters[fc == c].mean()) for c in range(3)},
         "wer": {codes[c].name: float(word_err[fc == c].mean()) for c in range(3)},
+        "tiles": {codes[c].name: tiles[c] for c in range(3)},
         "vs_plain": {
             "per_code_resident_launches": {"value": info / (ms_res / 1000.0), "ms_per_step": ms_res,
                                            "launches_per_step": 3},
@@ -341,6 +356,7 @@ def run_served(args):
     POOL = 2048
     pools = [I.awgn_llr(c, snr_rng.uniform(1.5, 4.5, POOL), POOL, 8 + 10 * k) for k, c in enumerate(codes)]
     p = lpdec.make_params(mu=MU, rho=RHO, eps=1e-5, max_iter=1000, state="f32", iters_per_launch=args.served_round)
+    tiles = autotune_codes(lpdec, handles, pools, "f32")
     srv = lpdec.Server(budget_bytes=8 << 30)
     ids = [srv.add_code(h) for h in handles]
     ptrs = [[pl[i].ctypes.data for i in range(POOL)] for pl in pools]
@@ -408,6 +424,7 @@ def run_served(args):
                    "frames": "2048 seeded frames per code, cycled"},
         "mean_iters": {names[c]: float(iters[which == c].mean()) for c in range(4)},
         "wer": {names[c]: float(err[which == c].mean()) for c in range(4)},
+        "tiles": {names[c]: tiles[c] for c in range(4)},
     }
     print(json.dumps(line), flush=True)
 

@@ -276,12 +276,15 @@ int device_sm_count(int device) {
 // Default tile: groups of at most 256 threads (each thread owns one check per
 // pass), as many groups per CTA as threads, named barriers and shared memory
 // allow.  Several frames per SM keep warps busy across the group barriers.
-Tile default_tile(const lpdec_code *c, int dtype) {
+Tile default_tile(const lpdec_code *c, int dtype, int max_threads) {
     Tile t;
-    const int maxT = class_max_threads(c->cls);
+    const int maxT = max_threads > 0 ? std::min(max_threads, class_max_threads(c->cls)) : class_max_threads(c->cls);
     const int lanes = class_lanes(kClassD[c->cls]);
     const long long slots = (long long)c->m * lanes;  // thread slots one pass over the checks needs
-    const int cap = std::min(256, maxT);
+    // One thread per check: several small groups per CTA (more frames in
+    // flight across the group barriers).  Segmented checks: one wide group,
+    // which measured fastest for the wide-check codes.
+    const int cap = lanes == 1 ? std::min(256, maxT) : maxT;
     const int passes = (int)((slots + cap - 1) / cap);
     int gt = (int)(((slots + passes - 1) / passes + 31) / 32 * 32);
     gt = std::max(32, std::min(gt, cap));
@@ -513,6 +516,104 @@ extern "C" int lpdec_decode_host(const lpdec_code *c, int32_t n_frames, const fl
     if (rc) return rc;
     if (e2 != cudaSuccess) return cuda_error(e2, "lpdec_decode_host: cudaFreeAsync");
     if (e3 != cudaSuccess) return cuda_error(e3, "lpdec_decode_host: cudaStreamSynchronize");
+    return LPDEC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: time candidate tiles on the caller's sample and keep the fastest
+
+extern "C" int lpdec_autotune(lpdec_code *c, const lpdec_params *p, int32_t n_frames, const float *llr,
+                              void *cuda_stream, int32_t *group_threads_out, int32_t *groups_out,
+                              double *ms_per_frame_out) {
+    if (!c || !llr) return set_error(LPDEC_EINVAL, "lpdec_autotune: code and llr must not be NULL");
+    if (n_frames < 1) return set_error(LPDEC_EINVAL, "lpdec_autotune: n_frames must be >= 1");
+    int rc = lpdec::validate_params(p);
+    if (rc) return rc;
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    lpdec_params q = *p;
+    q.schedule = LPDEC_SCHED_RESIDENT;
+    const int lanes = lpdec::class_lanes(lpdec::kClassD[c->cls]);
+    const int maxT = lpdec::class_max_threads(c->cls);
+    const int cap = lpdec::device_smem_optin(c->device);
+    std::vector<lpdec::Tile> cand;
+    for (int passes = 1; passes <= 12; ++passes) {
+        const long long slots = (long long)c->m * lanes;
+        int gt = (int)(((slots + passes - 1) / passes + 31) / 32 * 32);
+        if (gt > maxT || gt < 32) continue;
+        const lpdec::SliceLayout L = lpdec::slice_layout(c, q.state_dtype, gt);
+        const int gmax = std::min({15, maxT / gt, (int)(cap / L.bytes)});
+        for (int g = 1; g <= gmax; ++g) {
+            lpdec::Tile t;
+            t.group_threads = gt;
+            t.groups = g;
+            bool dup = false;
+            for (auto &o : cand) dup |= (o.group_threads == gt && o.groups == g);
+            if (!dup) cand.push_back(t);
+        }
+    }
+    if (cand.empty()) return set_error(LPDEC_EINVAL, "lpdec_autotune: no tile fits this code");
+    const size_t nx = (size_t)n_frames * c->n;
+    char *buf = nullptr;
+    const size_t wb = lpdec::workspace_bytes(c, n_frames, LPDEC_SCHED_RESIDENT, q.state_dtype, q.max_iter, 1);
+    cudaError_t err = cudaMallocAsync(reinterpret_cast<void **>(&buf), nx * 4 + 256 + wb, stream);
+    if (err != cudaSuccess) return cuda_error(err, "lpdec_autotune: cudaMallocAsync");
+    float *x = reinterpret_cast<float *>(buf);
+    void *work = buf + ((nx * 4 + 255) & ~(size_t)255);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 1e30;
+    lpdec::Tile best_t = cand[0];
+    rc = LPDEC_OK;
+    for (const auto &t : cand) {
+        rc = lpdec::enqueue_decode(c, n_frames, llr, &q, x, nullptr, nullptr, nullptr, stream, work,
+                                   LPDEC_SCHED_RESIDENT, t, nullptr);  // warm-up
+        if (rc) break;
+        cudaEventRecord(e0, stream);
+        for (int r = 0; r < 2 && !rc; ++r)
+            rc = lpdec::enqueue_decode(c, n_frames, llr, &q, x, nullptr, nullptr, nullptr, stream, work,
+                                       LPDEC_SCHED_RESIDENT, t, nullptr);
+        cudaEventRecord(e1, stream);
+        if (rc) break;
+        err = cudaEventSynchronize(e1);
+        if (err != cudaSuccess) { rc = cuda_error(err, "lpdec_autotune: timing"); break; }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = ms / 2.0 / n_frames;
+        if (per < best) { best = per; best_t = t; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(buf, stream);
+    cudaStreamSynchronize(stream);
+    if (rc) return rc;
+    best_t.valid = true;
+    c->tuned[q.state_dtype] = best_t;
+    if (group_threads_out) *group_threads_out = best_t.group_threads;
+    if (groups_out) *groups_out = best_t.groups;
+    if (ms_per_frame_out) *ms_per_frame_out = best;
+    return LPDEC_OK;
+}
+
+extern "C" int lpdec_set_tile(lpdec_code *c, int32_t state_dtype, int32_t group_threads, int32_t groups) {
+    if (!c) return set_error(LPDEC_EINVAL, "lpdec_set_tile: code is NULL");
+    if (state_dtype < 0 || state_dtype > 2) return set_error(LPDEC_EINVAL, "lpdec_set_tile: unknown state_dtype");
+    if (group_threads == 0 && groups == 0) {  // back to the built-in default
+        c->tuned[state_dtype] = lpdec::Tile();
+        return LPDEC_OK;
+    }
+    const int maxT = lpdec::class_max_threads(c->cls);
+    if (group_threads < 32 || group_threads % 32 || groups < 1 || groups > 15 || group_threads * groups > maxT)
+        return set_error(LPDEC_EINVAL, "lpdec_set_tile: %d groups x %d threads is not a valid tile", groups,
+                         group_threads);
+    const lpdec::SliceLayout L = lpdec::slice_layout(c, state_dtype, group_threads);
+    if ((int)(L.bytes * groups) > lpdec::device_smem_optin(c->device))
+        return set_error(LPDEC_EINVAL, "lpdec_set_tile: %d slices of %zu bytes exceed shared memory", groups, L.bytes);
+    lpdec::Tile t;
+    t.group_threads = group_threads;
+    t.groups = groups;
+    t.valid = true;
+    c->tuned[state_dtype] = t;
     return LPDEC_OK;
 }
 

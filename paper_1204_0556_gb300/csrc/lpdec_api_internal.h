@@ -28,7 +28,8 @@ int validate_params(const lpdec_params *p);
 IterCfg make_cfg(const lpdec_code *c, const lpdec_params *p);
 CodeView make_view(const lpdec_code *c);
 SliceLayout slice_layout(const lpdec_code *c, int dtype, int group_threads);
-Tile default_tile(const lpdec_code *c, int dtype);
+// max_threads > 0 caps the CTA size (kernels built for smaller CTAs).
+Tile default_tile(const lpdec_code *c, int dtype, int max_threads = 0);
 int device_smem_optin(int device);
 int device_sm_count(int device);
 int plan_launch(const lpdec_code *c, int dtype, const Tile &tile, int n_frames, cudaStream_t stream,

@@ -178,6 +178,7 @@ extern "C" int lpdec_decode_mixed(const lpdec_code *const *codes, int32_t n_code
     for (int c = 0; c < n_codes; ++c) {
         const lpdec_code *cc = codes[c];
         Tile tile = cc->tuned[p->state_dtype].valid ? cc->tuned[p->state_dtype] : default_tile(cc, p->state_dtype);
+        if (tile.group_threads > kMixedMaxThreads) tile = default_tile(cc, p->state_dtype, kMixedMaxThreads);
         if (tile.group_threads > kMixedMaxThreads)
             return set_error(LPDEC_EINVAL, "lpdec_decode_mixed: code %d needs %d threads per frame (limit %d)", c,
                              tile.group_threads, kMixedMaxThreads);

@@ -39,7 +39,7 @@ EXPORTED = [
     "lpdec_decode", "lpdec_decode_host", "lpdec_project", "lpdec_decode_noalloc",
     "lpdec_decode_mixed",
     "lpdec_server_create", "lpdec_server_add_code", "lpdec_server_submit", "lpdec_server_poll",
-    "lpdec_server_stats", "lpdec_server_destroy",
+    "lpdec_server_stats", "lpdec_server_destroy", "lpdec_autotune", "lpdec_set_tile",
 ]
 
 
@@ -105,6 +105,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
             "lpdec_server_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, _i32, _vp, _vp, _vp, _vp]),
             "lpdec_server_stats": (ctypes.c_int, [_vp, dp, dp, dp, ctypes.POINTER(_i64)]),
             "lpdec_server_destroy": (ctypes.c_int, [_vp]),
+            "lpdec_autotune": (ctypes.c_int, [_vp, P, _i32, _vp, _vp, _i32p, _i32p, dp]),
+            "lpdec_set_tile": (ctypes.c_int, [_vp, _i32, _i32, _i32]),
         })
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -220,6 +222,18 @@ def lpdec_server_stats(server: int) -> dict:
 
 def lpdec_server_destroy(server: int) -> None:
     _check(load().lpdec_server_destroy(server))
+
+
+def lpdec_autotune(handle: int, params, n_frames: int, llr_ptr: int, stream_ptr: int) -> dict:
+    gt, g = _i32(), _i32()
+    ms = ctypes.c_double()
+    _check(load().lpdec_autotune(handle, ctypes.byref(params), n_frames, llr_ptr, stream_ptr, ctypes.byref(gt),
+                                 ctypes.byref(g), ctypes.byref(ms)))
+    return {"group_threads": gt.value, "groups": g.value, "ms_per_frame": ms.value}
+
+
+def lpdec_set_tile(handle: int, state_dtype: int, group_threads: int, groups: int) -> None:
+    _check(load().lpdec_set_tile(handle, state_dtype, group_threads, groups))
 
 
 def lpdec_project(d, count, v_ptr, z_ptr, stream_ptr) -> None:
