@@ -536,7 +536,7 @@ extern "C" int lpdec_autotune(lpdec_code *c, const lpdec_params *p, int32_t n_fr
     const int maxT = lpdec::class_max_threads(c->cls);
     const int cap = lpdec::device_smem_optin(c->device);
     std::vector<lpdec::Tile> cand;
-    for (int passes = 1; passes <= 12; ++passes) {
+    for (int passes = 1; passes <= 32; ++passes) {
         const long long slots = (long long)c->m * lanes;
         int gt = (int)(((slots + passes - 1) / passes + 31) / 32 * 32);
         if (gt > maxT || gt < 32) continue;

@@ -421,10 +421,11 @@ __device__ __forceinline__ void check_update_seg(const CodeView &c, const IterCf
         g += ((th >> k) & 1u) ? zh : -zh;
     }
     g = seg_sum<L>(g);
-    bool done = !(d > 0 && g > (float)(ssz - 1));  // not violated: zh is the projection
+    const bool violated = d > 0 && g > (float)(ssz - 1);  // else zh is the projection
     float beta = 0.0f;
     {
         // fixed point of sum_k max(0, beta - kappa_k) = 1, from all entries active
+        bool done = !violated;
         float s1 = 0.0f;
         int c1 = 0;
 #pragma unroll
@@ -458,7 +459,7 @@ __device__ __forceinline__ void check_update_seg(const CodeView &c, const IterCf
             }
         }
         if (!done) beta = fmaxf(cur, 0.0f);
-        if (!(d > 0 && g > (float)(ssz - 1))) beta = 0.0f;
+        if (!violated) beta = 0.0f;
     }
     Proj pr;
     pr.facet = th;

@@ -15,7 +15,7 @@ namespace lpdec {
 namespace {
 constexpr int kD = LPDEC_D;
 constexpr int kL = class_lanes(kD);
-constexpr int kMaxT = 1024;
+constexpr int kMaxT = class_max_threads_D(kD);
 // Variable degree of the regular-code kernel built for this class (0: none).
 constexpr int kRegDV = kD == 6 ? 3 : (kD == 8 ? 4 : 0);
 

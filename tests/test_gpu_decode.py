@@ -158,9 +158,16 @@ def test_streamed_equals_resident(gpu, c1056, state):
         assert np.array_equal(a[k], c[k]), k
 
 
-@pytest.mark.parametrize("name,frames,iters", [("C2640", 8, 100), ("C4000", 8, 100), ("C8000", 6, 80)])
+def _shape(name):
+    if name == "S12":  # (3,12)-regular socket code: the 16-wide segmented check class
+        return I.socket_code(960, 3, [12] * 240, 4, name="S12")
+    return I.benchmark_code(name, 0)
+
+
+@pytest.mark.parametrize("name,frames,iters", [("C2640", 8, 100), ("C4000", 8, 100), ("C8000", 6, 80),
+                                               ("S12", 12, 100)])
 def test_other_code_shapes(gpu, oracle_mod, name, frames, iters):
-    code = I.benchmark_code(name, 0)
+    code = _shape(name)
     llr = I.awgn_llr(code, 3.0, frames, 303)
     kw = dict(mu=MU, rho=RHO, eps=0.0, max_iter=iters)
     got = gpu_decode(gpu, code, llr, **kw)
