@@ -825,9 +825,13 @@ namespace lpdec {
 // ---------------------------------------------------------------------------
 // Mixed-code batches: one persistent launch decodes frames of several codes.
 constexpr int kMaxMixedCodes = 8;
-// CTA size bound of the mixed kernel: holding every kernel form in one
-// function needs more than the 64 registers a 1024-thread CTA leaves.
-constexpr int kMixedMaxThreads = 768;
+// CTA size bound of the mixed kernel.  Each kernel form runs in its own
+// non-inlined function, so a 1024-thread CTA (64 registers) measured faster
+// than 768 threads with 80 registers.
+#ifndef LPDEC_MIXED_MAX_THREADS
+#define LPDEC_MIXED_MAX_THREADS 1024
+#endif
+constexpr int kMixedMaxThreads = LPDEC_MIXED_MAX_THREADS;
 
 // Kernel forms a code can run in (check degree class D, lanes per check L,
 // regular variable degree DV or 0).

@@ -31,7 +31,7 @@ inline int degree_class(int max_dc) {
 #ifndef LPDEC_L32
 #define LPDEC_L32 4
 #endif
-constexpr int class_lanes(int D) {
+__host__ __device__ constexpr int class_lanes(int D) {
     return D <= 8 ? 1 : (D <= 16 ? LPDEC_L16 : (D <= 20 ? LPDEC_L20 : LPDEC_L32));
 }
 

@@ -175,6 +175,7 @@ extern "C" int lpdec_decode_mixed(const lpdec_code *const *codes, int32_t n_code
     int block = 32;
     size_t smem = 0;
     const int cap = device_smem_optin(dev);
+    std::vector<SliceLayout> layouts((size_t)n_codes);
     for (int c = 0; c < n_codes; ++c) {
         const lpdec_code *cc = codes[c];
         Tile tile = cc->tuned[p->state_dtype].valid ? cc->tuned[p->state_dtype] : default_tile(cc, p->state_dtype);
@@ -182,22 +183,33 @@ extern "C" int lpdec_decode_mixed(const lpdec_code *const *codes, int32_t n_code
         if (tile.group_threads > kMixedMaxThreads)
             return set_error(LPDEC_EINVAL, "lpdec_decode_mixed: code %d needs %d threads per frame (limit %d)", c,
                              tile.group_threads, kMixedMaxThreads);
-        tile.groups = std::max(1, std::min(tile.groups, kMixedMaxThreads / tile.group_threads));
         const SliceLayout L = slice_layout(cc, p->state_dtype, tile.group_threads);
-        if ((int)(L.bytes * tile.groups) > cap)
+        if ((int)L.bytes > cap)
             return set_error(LPDEC_EINVAL, "lpdec_decode_mixed: code %d's frame state does not fit in shared memory", c);
+        layouts[c] = L;
         MixedCode &mc = a.code[c];
         mc.view = make_view(cc);
         mc.cfg = make_cfg(cc, p);
         mc.kind = kind_of(cc);
-        mc.groups = tile.groups;
         mc.group_threads = tile.group_threads;
         mc.smem_per_group = (int)L.bytes;
         mc.off_x = (int)L.off_x;
         mc.off_red = (int)L.off_red;
         mc.n_frames = (int)lists[c].size();
-        block = std::max(block, tile.groups * tile.group_threads);
-        smem = std::max(smem, L.bytes * tile.groups);
+        smem = std::max(smem, L.bytes);  // at least one frame of every code must fit in the CTA
+    }
+    // One CTA per SM serves every code in turn, so each code gets as many
+    // frames per CTA as the CTA's threads and shared memory allow (the CTA
+    // takes the largest single-code footprint, capped by the device).
+    for (int c = 0; c < n_codes; ++c) {
+        const int g = std::min(15, kMixedMaxThreads / a.code[c].group_threads);
+        smem = std::max(smem, std::min<size_t>((size_t)cap / layouts[c].bytes, (size_t)g) * layouts[c].bytes);
+    }
+    for (int c = 0; c < n_codes; ++c) {
+        MixedCode &mc = a.code[c];
+        const int g = std::min({15, kMixedMaxThreads / mc.group_threads, (int)(smem / layouts[c].bytes)});
+        mc.groups = std::max(1, g);
+        block = std::max(block, mc.groups * mc.group_threads);
     }
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
     const void *fn = mixed_fn(p->state_dtype);
