@@ -67,13 +67,31 @@ def dist_env():
     return ws, rank, local
 
 
+def workload_seeds(rank: int) -> list[int]:
+    """LLR seeds of one rank's batch (one per Eb/N0 point): ranks decode disjoint,
+    independent frames, so sharding needs no exchange of data."""
+    return [100 + p + 1000 * rank for p in range(len(SNRS))]
+
+
 def make_workload(frames_per_point: int, rank: int):
     from paper_1204_0556_gb300 import inputs as I
 
     code = I.benchmark_code("C1056", 0)
-    llr = np.concatenate([I.awgn_llr(code, snr, frames_per_point, 100 + p + 1000 * rank)
-                          for p, snr in enumerate(SNRS)])
+    llr = np.concatenate([I.awgn_llr(code, snr, frames_per_point, seed)
+                          for snr, seed in zip(SNRS, workload_seeds(rank))])
     return code, llr
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """The slowest rank's time (the job's time); identity without a process group."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def algorithmic_bytes_per_frame_iter(code, state_bytes: int) -> int:
@@ -530,12 +548,7 @@ def main():
             lpdec.decode(C, llr, p, stream=stream, out=out)
         e1.record(stream)
         barrier()
-        ms = e0.elapsed_time(e1) / steps
-        if ws > 1:
-            t = torch.tensor([ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(e0.elapsed_time(e1) / steps, dev)
 
     # ---- headline: timed region with clock sampling
     sampler = ClockSampler(local)
@@ -635,11 +648,7 @@ def main():
         for _ in range(args.steps):
             host_step()
         barrier()
-        e2e_s = (time.perf_counter() - t0) / args.steps
-        if ws > 1:
-            t = torch.tensor([e2e_s], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, dev)
         line["e2e"] = {"value": ws * F * code.k_design / e2e_s, "unit": UNIT,
                        "h2d_bytes_per_step": F * code.n * 4,
                        "d2h_bytes_per_step": F * code.n * 4 + F * code.n + F * 5,

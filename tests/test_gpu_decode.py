@@ -260,3 +260,30 @@ def test_wer_within_oracle_interval(gpu, oracle_mod, c1056):
     lo, hi = _wilson(k_ref, len(llr))
     assert lo <= k_gpu / len(llr) <= hi, (k_gpu, k_ref)
     assert k_ref >= 5
+
+
+def test_autotune_keeps_results(gpu, c1056):
+    """The autotuner changes only the tile; x and bits are those of the default tile
+    (each check and variable update is computed by one thread or lane segment in a
+    fixed order, whatever the tile)."""
+    import torch
+
+    llr = I.awgn_llr(c1056, 2.0, 64, 808)
+    C = gpu.Code(c1056)
+    try:
+        d_llr = torch.from_numpy(llr).cuda()
+        p = gpu.make_params(eps=0.0, max_iter=120)
+        a = {k: v.cpu().numpy() for k, v in gpu.decode(C, d_llr, p).items()}
+        t = gpu.lpdec_autotune(C.handle, p, 64, d_llr.data_ptr(), int(torch.cuda.current_stream().cuda_stream))
+        assert t["group_threads"] % 32 == 0 and t["groups"] >= 1
+        gpu.lpdec_set_tile(C.handle, 0, 32, 1)  # the narrowest tile as a second point
+        c = {k: v.cpu().numpy() for k, v in gpu.decode(C, d_llr, p).items()}
+        gpu.lpdec_set_tile(C.handle, 0, t["group_threads"], t["groups"])
+        b = {k: v.cpu().numpy() for k, v in gpu.decode(C, d_llr, p).items()}
+        torch.cuda.synchronize()
+        for k in ("x", "bits", "iters"):
+            assert np.array_equal(a[k], b[k]) and np.array_equal(a[k], c[k]), k
+        with pytest.raises(gpu.LpdecError):
+            gpu.lpdec_set_tile(C.handle, 0, 48, 1)  # not a whole number of warps
+    finally:
+        C.close()
