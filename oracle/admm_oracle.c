@@ -75,31 +75,31 @@ static void sort_asc(int n, double *a)
     }
 }
 
-/* Steps shared by both projection routes: Algorithm 2 lines 1-16.
+/* Steps shared by both projection routes: Algorithm 2 up to the breakpoint search.
  * Returns 1 when the projection is zhat (written to z in the original order),
  * 0 when beta_opt must still be found; v, q, r and beta_max are filled. */
 static int project_prefix(int d, const double *u, double *z, double *v, int *q,
                           int *r_out, double *beta_max_out)
 {
-    /* line 1: sort descending, v = Q u (q[k] = original index of v[k]) */
+    /* sort descending, v = Q u (q[k] = original index of v[k]) */
     sort_desc_idx(d, u, q);
     for (int k = 0; k < d; ++k) v[k] = u[q[k]];
-    /* line 2: zhat = Pi_[0,1](v) */
+    /* zhat = Pi_[0,1](v) */
     double zhat[ORACLE_MAX_D];
     double s = 0.0;
     for (int k = 0; k < d; ++k) { zhat[k] = clip01(v[k]); s += zhat[k]; }
-    /* line 3: r = even floor of ||zhat||_1 */
+    /* r = even floor of ||zhat||_1 (the constituent parity, Lemma 3) */
     int r = 2 * (int)floor(s / 2.0);
     if (r > d) r = d - (d & 1); /* guard against rounding; s <= d always */
     *r_out = r;
-    /* lines 4-6 */
+    /* r = d: zhat is the projection */
     if (r == d) {
         for (int k = 0; k < d; ++k) z[q[k]] = zhat[k];
         return 1;
     }
-    /* lines 7-11 (1-based v_{r+1}, v_{r+2} are v[r], v[r+1] here) */
+    /* beta_max (Lemma 4); the 1-based v_{r+1}, v_{r+2} are v[r], v[r+1] here */
     *beta_max_out = (r <= d - 2) ? 0.5 * (v[r] - v[r + 1]) : v[r];
-    /* lines 12-15: f_r^T zhat <= r  ->  zhat is the projection */
+    /* f_r^T zhat <= r  ->  zhat is the projection (eq. (fr-def), Lemma 4) */
     double g0 = 0.0;
     for (int k = 0; k < d; ++k) g0 += f_r(k, r) * zhat[k];
     if (g0 <= (double)r) {
@@ -157,7 +157,7 @@ int oracle_project(int d, const double *u, double *z)
     if (beta < lo) beta = lo;
     if (beta > hi) beta = hi;
 
-    /* last line: z* = Q^T Pi_[0,1](v - beta_opt f_r) */
+    /* return z* = Q^T Pi_[0,1](v - beta_opt f_r) */
     for (int k = 0; k < d; ++k) z[q[k]] = clip01(v[k] - beta * f_r(k, r));
     return 0;
 }
@@ -225,17 +225,17 @@ int oracle_decode(int n, int m, const int32_t *row_ptr, const int32_t *col_idx,
     const double eps_c = eps > 1e-5 ? eps : 1e-5;
     for (int f = f_lo; f < f_hi; ++f) {
         const double *g = gamma + (size_t)f * (size_t)n;
-        /* Algorithm 1 line 2: z_j = lambda_j = 0 */
+        /* Algorithm 1 initialization: z_j = lambda_j = 0 */
         for (int e = 0; e < E; ++e) { z[e] = 0.0; lam[e] = 0.0; }
         int k = 0, converged = 0;
         double Rp = 0.0, Rd = 0.0;
         while (k < max_iter) {
-            /* lines 4-6: x_i = Pi_[0,1]( (sum_{j in N_v(i)} (z_j^(i) - lambda_j^(i)/mu)
+            /* x-update (Section 3.2): x_i = Pi_[0,1]( (sum_{j in N_v(i)} (z_j^(i) - lambda_j^(i)/mu)
              *                            - gamma_i/mu) / |N_v(i)| ) */
             for (int i = 0; i < n; ++i) acc[i] = 0.0;
             for (int e = 0; e < E; ++e) acc[col_idx[e]] += z[e] - lam[e] / mu;
             for (int i = 0; i < n; ++i) x[i] = clip01((acc[i] - g[i] / mu) / deg[i]);
-            /* lines 7-11, over-relaxed: for each check j */
+            /* z- and lambda-updates, over-relaxed (Section 5.2): for each check j */
             Rp = 0.0;
             Rd = 0.0;
             for (int j = 0; j < m; ++j) {
@@ -258,7 +258,7 @@ int oracle_decode(int n, int m, const int32_t *row_ptr, const int32_t *col_idx,
                 }
             }
             ++k;
-            /* line 13: stop when both residuals are below eps^2 E */
+            /* stopping test (Section 3.3): both residuals below eps^2 E */
             if (eps > 0.0 && Rp < eps * eps * (double)E && Rd < eps * eps * (double)E) {
                 converged = 1;
                 break;

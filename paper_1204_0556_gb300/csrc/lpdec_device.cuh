@@ -592,7 +592,7 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
     if (t == 0) { flags[0] = 0; flags[1] = 0; flags[2] = 0; }
 
     if (k == 0) {
-        // Algorithm 1 line 2: z = lambda = 0.  Also reject non-finite LLRs.
+        // Algorithm 1 initialization: z = lambda = 0.  Also reject non-finite LLRs.
         int bad = 0;
         for (int i = t; i < c.n; i += T) bad |= !isfinite(__ldg(gam + i));
         zero16(sm.z, 2 * state_bytes, t, T);
@@ -640,7 +640,7 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
     const int k_end = min(p.max_iter, k + iters_this_launch);
     bool conv = false, rok = false;
     while (k < k_end) {
-        // ---- x-update (Algorithm 1 lines 4-6; Section 3.2)
+        // ---- x-update (Algorithm 1; Section 3.2)
         for (int i = t; i < c.n; i += T) {
             float acc = 0.0f, inv_dv;
             if constexpr (DV > 0) {
@@ -662,7 +662,7 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
             sm.x[i] = __saturatef((acc - gi * p.mu_inv) * inv_dv);
         }
         group_sync(bar, T);
-        // ---- z- and lambda-updates (Algorithm 1 lines 7-11)
+        // ---- z- and lambda-updates (Algorithm 1; Section 5.2 over-relaxation)
         const bool need_res = p.check_stop || (k + 1 == p.max_iter);
         float rp = 0.0f, rd = 0.0f;
         if constexpr (L == 1) {
@@ -676,7 +676,7 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
         }
         ++k;
         if (need_res) {
-            // ---- stopping test (Algorithm 1 line 13)
+            // ---- stopping test (Algorithm 1; Section 3.3)
             rp = warp_sum(rp);
             rd = warp_sum(rd);
             if (lane == 0) { sm.red[2 * w] = rp; sm.red[2 * w + 1] = rd; }
