@@ -134,6 +134,35 @@ def algorithmic_ops_per_frame_iter(code) -> int:
     return ops
 
 
+# DRAM traffic of the decode kernel per frame, from one ncu capture of the small
+# bench case (dram__bytes_read.sum + dram__bytes_write.sum over the frames of
+# that launch; traffic grows with the number of frames).  Keyed by a hash of the
+# kernel sources: a changed kernel reports null until it is captured again.
+KERNEL_SOURCES = ("lpdec_device.cuh", "lpdec_kclass.cuh", "lpdec_internal.h")
+MEASURED_TRAFFIC = {
+    # schedule: (source hash, bytes per frame per launch, capture)
+    "resident": None,
+    "streamed": None,
+}
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1204_0556_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(schedule: str, frames: int):
+    rec = MEASURED_TRAFFIC.get(schedule)
+    if not rec or rec[0] != kernel_source_hash():
+        return None
+    return int(rec[1] * frames)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -577,7 +606,7 @@ def main():
         ach_gops = F * ITERS * ops / (launch_ms / 1000.0) / 1e9
         roofline = {
             "bound": "alu", "achieved": round(ach_gops, 1), "peak": round(peak_gops, 1), "unit": "Gop/s",
-            "frac": round(ach_gops / peak_gops, 4), "traffic": None, "kernel": kname,
+            "frac": round(ach_gops / peak_gops, 4), "traffic": traffic_per_launch("resident", F), "kernel": kname,
             "note": f"{ops} algorithmic FP32 ops per frame-iteration x {F} frames x {ITERS} iterations per "
                     f"launch; peak = 152 SMs x 128 lanes x {sm_max:.0f} MHz",
             "hbm_effective": {"achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
@@ -588,7 +617,7 @@ def main():
     else:
         roofline = {
             "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-            "frac": round(achieved / hbm_peak, 4), "traffic": None, "kernel": kname,
+            "frac": round(achieved / hbm_peak, 4), "traffic": traffic_per_launch("streamed", F), "kernel": kname,
             "note": f"peak is the {peak_kind} HBM copy bandwidth; algorithmic bytes {B} per frame-iteration "
                     f"x {F} frames x {ITERS // launches_per_step} iterations per launch",
         }
