@@ -141,8 +141,10 @@ def algorithmic_ops_per_frame_iter(code) -> int:
 KERNEL_SOURCES = ("lpdec_device.cuh", "lpdec_kclass.cuh", "lpdec_internal.h")
 MEASURED_TRAFFIC = {
     # schedule: (source hash, bytes per frame per launch, capture)
-    "resident": None,
-    "streamed": None,
+    "resident": ("cbf0bc36e1fe37e2", (33_849_088 + 1_634_560) / 8000,
+                 "profiles/decode_kernel_resident_C1056_small.md: 8000 frames x 300 iterations in one launch"),
+    "streamed": ("cbf0bc36e1fe37e2", (236_719_872 + 141_154_304) / 8000,
+                 "profiles/decode_kernel_streamed_C1056_small.md: one iteration of 8000 frames per launch"),
 }
 
 
