@@ -44,6 +44,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--frames-per-point", type=int, default=10_000)
+    ap.add_argument("--code", default="C1056", choices=["C96", "C1056", "C2640", "C4000", "C8000"],
+                    help="code of the single-code workload (the headline is C1056)")
+    ap.add_argument("--iters", type=int, default=300, help="fixed ADMM iterations of the single-code workload")
+    ap.add_argument("--no-autotune", action="store_true", help="use the library's default tile")
     ap.add_argument("--schedule", default="resident", choices=["resident", "streamed", "auto"])
     ap.add_argument("--state", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--variants", type=int, default=1, help="also time the other schedules/precisions")
@@ -73,10 +77,13 @@ def workload_seeds(rank: int) -> list[int]:
     return [100 + p + 1000 * rank for p in range(len(SNRS))]
 
 
-def make_workload(frames_per_point: int, rank: int):
+CODE_SEEDS = {"C96": 0, "C1056": 0, "C2640": 1, "C4000": 2, "C8000": 3}
+
+
+def make_workload(frames_per_point: int, rank: int, name: str = "C1056"):
     from paper_1204_0556_gb300 import inputs as I
 
-    code = I.benchmark_code("C1056", 0)
+    code = I.benchmark_code(name, CODE_SEEDS[name])
     llr = np.concatenate([I.awgn_llr(code, snr, frames_per_point, seed)
                           for snr, seed in zip(SNRS, workload_seeds(rank))])
     return code, llr
@@ -140,10 +147,10 @@ def algorithmic_ops_per_frame_iter(code) -> int:
 # kernel sources: a changed kernel reports null until it is captured again.
 KERNEL_SOURCES = ("lpdec_device.cuh", "lpdec_kclass.cuh", "lpdec_internal.h")
 MEASURED_TRAFFIC = {
-    # schedule: (source hash, bytes per frame per launch, capture)
-    "resident": ("cbf0bc36e1fe37e2", (33_849_088 + 1_634_560) / 8000,
+    # "code/schedule": (source hash, bytes per frame per launch, capture)
+    "C1056/resident": ("cbf0bc36e1fe37e2", (33_849_088 + 1_634_560) / 8000,
                  "profiles/decode_kernel_resident_C1056_small.md: 8000 frames x 300 iterations in one launch"),
-    "streamed": ("cbf0bc36e1fe37e2", (236_719_872 + 141_154_304) / 8000,
+    "C1056/streamed": ("cbf0bc36e1fe37e2", (236_719_872 + 141_154_304) / 8000,
                  "profiles/decode_kernel_streamed_C1056_small.md: one iteration of 8000 frames per launch"),
 }
 
@@ -158,8 +165,8 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch(schedule: str, frames: int):
-    rec = MEASURED_TRAFFIC.get(schedule)
+def traffic_per_launch(key: str, frames: int):
+    rec = MEASURED_TRAFFIC.get(key)
     if not rec or rec[0] != kernel_source_hash():
         return None
     return int(rec[1] * frames)
@@ -247,7 +254,7 @@ def oracle_sample(code, llr, seconds: float):
                   max_iter=ITERS, threads=threads)
     dt = time.perf_counter() - t0
     return {"value": n * code.k_design / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{n} of {F} frames (evenly spaced over the 4 Eb/N0 points), 300 iterations each, "
+            "sample": f"{n} of {F} frames (evenly spaced over the 4 Eb/N0 points), {ITERS} iterations each, "
                       f"FP64, {threads} threads", "seconds": round(dt, 2)}
 
 
@@ -549,9 +556,17 @@ def main():
     build.build()
     lpdec.load()
 
-    code, llr_h = make_workload(args.frames_per_point, rank)
+    global ITERS
+    ITERS = args.iters
+    code, llr_h = make_workload(args.frames_per_point, rank, args.code)
     F = len(llr_h)
     C = lpdec.Code(code)
+    tile = None
+    if not args.no_autotune:
+        sample = torch.from_numpy(np.ascontiguousarray(llr_h[:: max(1, F // 2048)][:2048])).cuda()
+        tile = lpdec.lpdec_autotune(C.handle, lpdec.make_params(mu=MU, rho=RHO, eps=0.0, max_iter=60,
+                                                                 state=args.state, schedule="resident"),
+                                    sample.shape[0], sample.data_ptr(), int(torch.cuda.current_stream().cuda_stream))
     dev = torch.device("cuda", local)
     llr = torch.from_numpy(llr_h).to(dev)
     out = {
@@ -597,7 +612,7 @@ def main():
     launch_ms = ms / launches_per_step
     hbm_peak, peak_kind = measured_peaks()
     achieved = bytes_per_launch / (launch_ms / 1000.0) / 1e9
-    kname = f"lpdec::decode_kernel<6,1,3,{args.state}> ({args.schedule})"
+    kname = f"lpdec::decode_kernel ({code.name}, {args.state}, {args.schedule})"
     if args.schedule in ("resident", "auto"):
         # State stays in shared memory for all 300 iterations: the kernel is bound
         # by instruction issue, not HBM.  Peak: 152 SMs x 128 FP32 lanes x the
@@ -608,7 +623,7 @@ def main():
         ach_gops = F * ITERS * ops / (launch_ms / 1000.0) / 1e9
         roofline = {
             "bound": "alu", "achieved": round(ach_gops, 1), "peak": round(peak_gops, 1), "unit": "Gop/s",
-            "frac": round(ach_gops / peak_gops, 4), "traffic": traffic_per_launch("resident", F), "kernel": kname,
+            "frac": round(ach_gops / peak_gops, 4), "traffic": traffic_per_launch(f"{code.name}/resident", F), "kernel": kname,
             "note": f"{ops} algorithmic FP32 ops per frame-iteration x {F} frames x {ITERS} iterations per "
                     f"launch; peak = 152 SMs x 128 lanes x {sm_max:.0f} MHz",
             "hbm_effective": {"achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
@@ -619,7 +634,7 @@ def main():
     else:
         roofline = {
             "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-            "frac": round(achieved / hbm_peak, 4), "traffic": traffic_per_launch("streamed", F), "kernel": kname,
+            "frac": round(achieved / hbm_peak, 4), "traffic": traffic_per_launch(f"{code.name}/streamed", F), "kernel": kname,
             "note": f"peak is the {peak_kind} HBM copy bandwidth; algorithmic bytes {B} per frame-iteration "
                     f"x {F} frames x {ITERS // launches_per_step} iterations per launch",
         }
@@ -630,14 +645,16 @@ def main():
         wer[str(snr)] = float(bits_h[p * per:(p + 1) * per].any(axis=1).mean())
 
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "metric": METRIC if code.name == "C1056" else METRIC.replace("(3,6) n=1056", code.name), "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": args.state, "data": "synthetic",
-        "config": {"workload": f"C1056 (3,6) n=1056 m=528 Gallager seed 0, 4-cycle free; {F} frames "
-                               f"({per} at each of 1.5/2.0/2.5/3.0 dB), mu=3 rho=1.9, 300 fixed iterations, "
+        "config": {"workload": f"{code.name}: n={code.n} m={code.m} seed {CODE_SEEDS[code.name]}"
+                               f"{', 4-cycle free' if code.name in ('C1056', 'C2640') else ''}; {F} frames "
+                               f"({per} at each of 1.5/2.0/2.5/3.0 dB), mu=3 rho=1.9, {ITERS} fixed iterations, "
                                f"FP32 arithmetic, {args.state} z/lambda state",
-                   "schedule": args.schedule, "frames_per_step": F * ws,
-                   "l2": "inputs larger than L2: 169 MB of LLRs read and 169 MB of x written per step",
+                   "schedule": args.schedule, "frames_per_step": F * ws, "tile": tile,
+                   "l2": f"inputs larger than L2: {F * code.n * 4 / 1e6:.0f} MB of LLRs read and "
+                         f"{F * code.n * 4 / 1e6:.0f} MB of x written per step",
                    "parallelism": f"frames sharded over {ws} rank(s), no collective on the data path"},
         "frames_per_s": ws * F / (ms / 1000.0),
         "wer": wer, "certified_frac": float(cert_h.mean()),
