@@ -274,6 +274,11 @@ LPDEC_API int lpdec_server_poll(lpdec_server *server, uint64_t request_id, int32
 LPDEC_API int lpdec_server_stats(lpdec_server *server, double *p50_ms, double *p99_ms, double *bits_per_s,
                                  int64_t *frames);
 
+/* Scheduler accounting: rounds run, their total host wall time, and their total
+ * device time (first launch to last launch of each round).  Any pointer may be NULL. */
+LPDEC_API int lpdec_server_counters(lpdec_server *server, int64_t *rounds, double *round_wall_ms,
+                                    double *round_gpu_ms);
+
 /* Stop accepting requests, finish the frames already submitted, free the
  * server.  Calls racing with destroy on other threads get LPDEC_ECLOSED. */
 LPDEC_API int lpdec_server_destroy(lpdec_server *server);

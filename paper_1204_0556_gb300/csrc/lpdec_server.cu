@@ -138,6 +138,11 @@ struct lpdec_server {
     double info_bits = 0.0;
     lpdec::Clock::time_point t_first, t_last;
     bool have_first = false;
+    // round accounting
+    int64_t rounds = 0;
+    double round_wall_ms = 0.0;  // host time of whole rounds
+    double round_gpu_ms = 0.0;   // device time from the first to the last launch of a round
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
 namespace lpdec {
@@ -209,6 +214,8 @@ int pool_alloc(lpdec_server *sv, Pool &P, int slots) {
 
 // One scheduling round.  Returns an LPDEC status; the caller holds no lock.
 int run_round(lpdec_server *sv) {
+    const auto t_round = Clock::now();
+    bool timed = false;
     // ---- 1. admission (under the lock)
     {
         std::lock_guard<std::mutex> lk(sv->mu);
@@ -238,6 +245,10 @@ int run_round(lpdec_server *sv) {
     for (auto &pp : sv->pools) {
         Pool &P = *pp;
         if (P.active.empty()) continue;
+        if (!timed && sv->ev0) {
+            cudaEventRecord(sv->ev0, sv->stream);
+            timed = true;
+        }
         const int n = P.code->n;
         if (P.n_new > 0) {
             err = cudaMemcpyAsync(P.d_new_llr, P.h_new_llr, (size_t)P.n_new * n * 4, cudaMemcpyHostToDevice, sv->stream);
@@ -274,8 +285,11 @@ int run_round(lpdec_server *sv) {
         err = cudaMemcpyAsync(P.h_kc, P.d_kc, (size_t)na * 4, cudaMemcpyDeviceToHost, sv->stream);
         if (err != cudaSuccess) return cuda_error(err, "server: status copy");
     }
+    if (timed) cudaEventRecord(sv->ev1, sv->stream);
     err = cudaStreamSynchronize(sv->stream);
     if (err != cudaSuccess) return cuda_error(err, "server: round");
+    float gpu_ms = 0.0f;
+    if (timed) cudaEventElapsedTime(&gpu_ms, sv->ev0, sv->ev1);
     // ---- 3. finished frames: gather and copy their outputs
     std::vector<int> nfin(sv->pools.size(), 0);
     for (size_t pi = 0; pi < sv->pools.size(); ++pi) {
@@ -337,6 +351,9 @@ int run_round(lpdec_server *sv) {
             P.active.swap(keep);
         }
         if (any_done) sv->cv_done.notify_all();
+        sv->rounds += 1;
+        sv->round_gpu_ms += gpu_ms;
+        sv->round_wall_ms += std::chrono::duration<double, std::milli>(Clock::now() - t_round).count();
     }
     return LPDEC_OK;
 }
@@ -384,6 +401,8 @@ extern "C" int lpdec_server_create(size_t device_budget_bytes, void *cuda_stream
         return lpdec::cuda_error(err, "lpdec_server_create: cudaGetDevice");
     }
     sv->budget = device_budget_bytes;
+    cudaEventCreate(&sv->ev0);
+    cudaEventCreate(&sv->ev1);
     if (cuda_stream) {
         sv->stream = static_cast<cudaStream_t>(cuda_stream);
     } else {
@@ -521,6 +540,16 @@ extern "C" int lpdec_server_stats(lpdec_server *sv, double *p50_ms, double *p99_
     return LPDEC_OK;
 }
 
+extern "C" int lpdec_server_counters(lpdec_server *sv, int64_t *rounds, double *round_wall_ms,
+                                     double *round_gpu_ms) {
+    if (!sv) return set_error(LPDEC_EINVAL, "lpdec_server_counters: server is NULL");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (rounds) *rounds = sv->rounds;
+    if (round_wall_ms) *round_wall_ms = sv->round_wall_ms;
+    if (round_gpu_ms) *round_gpu_ms = sv->round_gpu_ms;
+    return LPDEC_OK;
+}
+
 extern "C" int lpdec_server_destroy(lpdec_server *sv) {
     if (!sv) return set_error(LPDEC_EINVAL, "lpdec_server_destroy: server is NULL");
     {
@@ -536,6 +565,8 @@ extern "C" int lpdec_server_destroy(lpdec_server *sv) {
         if (pp->host && cudaFreeHost(pp->host) != cudaSuccess) rc = LPDEC_ECUDA;
     }
     if (sv->own_stream) cudaStreamDestroy(sv->stream);
+    if (sv->ev0) cudaEventDestroy(sv->ev0);
+    if (sv->ev1) cudaEventDestroy(sv->ev1);
     delete sv;
     if (rc) return set_error(rc, "lpdec_server_destroy: freeing device memory failed");
     return LPDEC_OK;

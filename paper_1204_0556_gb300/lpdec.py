@@ -39,7 +39,7 @@ EXPORTED = [
     "lpdec_decode", "lpdec_decode_host", "lpdec_project", "lpdec_decode_noalloc",
     "lpdec_decode_mixed",
     "lpdec_server_create", "lpdec_server_add_code", "lpdec_server_submit", "lpdec_server_poll",
-    "lpdec_server_stats", "lpdec_server_destroy", "lpdec_autotune", "lpdec_set_tile",
+    "lpdec_server_stats", "lpdec_server_destroy", "lpdec_autotune", "lpdec_set_tile", "lpdec_server_counters",
 ]
 
 
@@ -105,6 +105,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
             "lpdec_server_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, _i32, _vp, _vp, _vp, _vp]),
             "lpdec_server_stats": (ctypes.c_int, [_vp, dp, dp, dp, ctypes.POINTER(_i64)]),
             "lpdec_server_destroy": (ctypes.c_int, [_vp]),
+            "lpdec_server_counters": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), dp, dp]),
             "lpdec_autotune": (ctypes.c_int, [_vp, P, _i32, _vp, _vp, _i32p, _i32p, dp]),
             "lpdec_set_tile": (ctypes.c_int, [_vp, _i32, _i32, _i32]),
         })
@@ -218,6 +219,13 @@ def lpdec_server_stats(server: int) -> dict:
     _check(load().lpdec_server_stats(server, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(bps),
                                      ctypes.byref(fr)))
     return {"p50_ms": p50.value, "p99_ms": p99.value, "bits_per_s": bps.value, "frames": fr.value}
+
+
+def lpdec_server_counters(server: int) -> dict:
+    r = _i64()
+    w, g = ctypes.c_double(), ctypes.c_double()
+    _check(load().lpdec_server_counters(server, ctypes.byref(r), ctypes.byref(w), ctypes.byref(g)))
+    return {"rounds": r.value, "round_wall_ms": w.value, "round_gpu_ms": g.value}
 
 
 def lpdec_server_destroy(server: int) -> None:
@@ -367,6 +375,9 @@ class Server:
 
     def stats(self) -> dict:
         return lpdec_server_stats(self.handle)
+
+    def counters(self) -> dict:
+        return lpdec_server_counters(self.handle)
 
     def close(self):
         if self.handle:
