@@ -239,7 +239,9 @@ LPDEC_API int lpdec_decode_noalloc(const lpdec_code *code, int32_t n_frames, con
  * are on the GPU join the next round.  A frame's result is identical to
  * lpdec_decode of that frame alone.
  *   device_budget_bytes: upper bound on the device memory of all slot pools.
- *   cuda_stream: stream for the server's work, or NULL for a private stream.
+ *   cuda_stream: work already queued on this stream (NULL: the legacy default
+ *                stream) completes before a code's first round; each code's
+ *                rounds then run on a private stream, so codes overlap on the GPU.
  */
 LPDEC_API int lpdec_server_create(size_t device_budget_bytes, void *cuda_stream, lpdec_server **out);
 
@@ -275,7 +277,8 @@ LPDEC_API int lpdec_server_stats(lpdec_server *server, double *p50_ms, double *p
                                  int64_t *frames);
 
 /* Scheduler accounting: rounds run, their total host wall time, and their total
- * device time (first launch to last launch of each round).  Any pointer may be NULL. */
+ * device time (per round, the slowest code's first-to-last launch span).  Any
+ * pointer may be NULL. */
 LPDEC_API int lpdec_server_counters(lpdec_server *server, int64_t *rounds, double *round_wall_ms,
                                     double *round_gpu_ms);
 

@@ -8,7 +8,8 @@
 //      kernel that places them and marks the slots fresh;
 //   2. advance every active slot of every code by `iters_per_launch` ADMM
 //      iterations with the decode kernel (STREAMED form, indexed by a slot
-//      list): frames admitted this round and frames in flight share the launch;
+//      list): frames admitted this round and frames in flight share the launch,
+//      and each code's launches run on a stream of their own so codes overlap;
 //   3. read back which slots finished (converged or reached max_iter), gather
 //      their outputs into one compact buffer, copy it to the host, free the
 //      slots and complete requests whose frames are all done.
@@ -109,6 +110,9 @@ struct Pool {
     std::vector<std::pair<Request *, int>> owner;
     std::deque<Request *> pending;
     int n_new = 0;
+    cudaStream_t stream = nullptr;  // this code's rounds run here, overlapping the other codes
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool timed = false;
 };
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -141,8 +145,7 @@ struct lpdec_server {
     // round accounting
     int64_t rounds = 0;
     double round_wall_ms = 0.0;  // host time of whole rounds
-    double round_gpu_ms = 0.0;   // device time from the first to the last launch of a round
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    double round_gpu_ms = 0.0;   // device time of a round: its slowest code, first launch to last
 };
 
 namespace lpdec {
@@ -204,6 +207,22 @@ int pool_alloc(lpdec_server *sv, Pool &P, int slots) {
     P.h_bo = reinterpret_cast<uint8_t *>(h + h_bo);
     P.h_io = reinterpret_cast<int32_t *>(h + h_io);
     P.h_co = reinterpret_cast<uint8_t *>(h + h_co);
+    err = cudaStreamCreateWithFlags(&P.stream, cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaEventCreate(&P.ev0);
+    if (err == cudaSuccess) err = cudaEventCreate(&P.ev1);
+    if (err != cudaSuccess) {
+        cudaFree(P.dev);
+        cudaFreeHost(P.host);
+        P.dev = P.host = nullptr;
+        return cuda_error(err, "lpdec_server_add_code: stream creation");
+    }
+    // the code's first round follows whatever the caller queued on the server stream
+    cudaEvent_t after;
+    if (cudaEventCreateWithFlags(&after, cudaEventDisableTiming) == cudaSuccess) {
+        cudaEventRecord(after, sv->stream);
+        cudaStreamWaitEvent(P.stream, after, 0);
+        cudaEventDestroy(after);
+    }
     P.cap = slots;
     P.free_slots.resize(slots);
     for (int s = 0; s < slots; ++s) P.free_slots[s] = slots - 1 - s;
@@ -215,7 +234,6 @@ int pool_alloc(lpdec_server *sv, Pool &P, int slots) {
 // One scheduling round.  Returns an LPDEC status; the caller holds no lock.
 int run_round(lpdec_server *sv) {
     const auto t_round = Clock::now();
-    bool timed = false;
     // ---- 1. admission (under the lock)
     {
         std::lock_guard<std::mutex> lk(sv->mu);
@@ -240,28 +258,28 @@ int run_round(lpdec_server *sv) {
             }
         }
     }
-    // ---- 2. device work for every pool with frames in flight
+    // ---- 2. device work for every pool with frames in flight, each on its own
+    // stream so the codes' launches overlap
     cudaError_t err;
     for (auto &pp : sv->pools) {
         Pool &P = *pp;
+        P.timed = false;
         if (P.active.empty()) continue;
-        if (!timed && sv->ev0) {
-            cudaEventRecord(sv->ev0, sv->stream);
-            timed = true;
-        }
+        cudaStream_t st = P.stream;
+        cudaEventRecord(P.ev0, st);
+        P.timed = true;
         const int n = P.code->n;
         if (P.n_new > 0) {
-            err = cudaMemcpyAsync(P.d_new_llr, P.h_new_llr, (size_t)P.n_new * n * 4, cudaMemcpyHostToDevice, sv->stream);
+            err = cudaMemcpyAsync(P.d_new_llr, P.h_new_llr, (size_t)P.n_new * n * 4, cudaMemcpyHostToDevice, st);
             if (err == cudaSuccess)
-                err = cudaMemcpyAsync(P.d_new_slots, P.h_new_slots, (size_t)P.n_new * 4, cudaMemcpyHostToDevice,
-                                      sv->stream);
+                err = cudaMemcpyAsync(P.d_new_slots, P.h_new_slots, (size_t)P.n_new * 4, cudaMemcpyHostToDevice, st);
             if (err != cudaSuccess) return cuda_error(err, "server: admission copy");
-            scatter_new_frames<<<P.n_new, 128, 0, sv->stream>>>(n, P.n_new, P.d_new_slots, P.d_new_llr, P.llr, P.kst);
+            scatter_new_frames<<<P.n_new, 128, 0, st>>>(n, P.n_new, P.d_new_slots, P.d_new_llr, P.llr, P.kst);
         }
         const int na = (int)P.active.size();
         std::memcpy(P.h_active, P.active.data(), (size_t)na * 4);
-        err = cudaMemcpyAsync(P.d_active, P.h_active, (size_t)na * 4, cudaMemcpyHostToDevice, sv->stream);
-        if (err == cudaSuccess) err = cudaMemsetAsync(P.d_queue, 0, 4, sv->stream);
+        err = cudaMemcpyAsync(P.d_active, P.h_active, (size_t)na * 4, cudaMemcpyHostToDevice, st);
+        if (err == cudaSuccess) err = cudaMemsetAsync(P.d_queue, 0, 4, st);
         if (err != cudaSuccess) return cuda_error(err, "server: round set-up");
         DecodeArgs a;
         std::memset(&a, 0, sizeof(a));
@@ -279,17 +297,23 @@ int run_round(lpdec_server *sv) {
         a.iters_this_launch = P.params.iters_per_launch;
         a.frame_list = P.d_active;
         a.queue = P.d_queue;
-        int rc = launch_once(P.code, P.params.state_dtype, P.tile, a, sv->stream);
+        int rc = launch_once(P.code, P.params.state_dtype, P.tile, a, st);
         if (rc) return rc;
-        gather_k_state<<<(na + 255) / 256, 256, 0, sv->stream>>>(na, P.d_active, P.kst, P.d_kc);
-        err = cudaMemcpyAsync(P.h_kc, P.d_kc, (size_t)na * 4, cudaMemcpyDeviceToHost, sv->stream);
+        gather_k_state<<<(na + 255) / 256, 256, 0, st>>>(na, P.d_active, P.kst, P.d_kc);
+        cudaEventRecord(P.ev1, st);
+        err = cudaMemcpyAsync(P.h_kc, P.d_kc, (size_t)na * 4, cudaMemcpyDeviceToHost, st);
         if (err != cudaSuccess) return cuda_error(err, "server: status copy");
     }
-    if (timed) cudaEventRecord(sv->ev1, sv->stream);
-    err = cudaStreamSynchronize(sv->stream);
-    if (err != cudaSuccess) return cuda_error(err, "server: round");
     float gpu_ms = 0.0f;
-    if (timed) cudaEventElapsedTime(&gpu_ms, sv->ev0, sv->ev1);
+    for (auto &pp : sv->pools) {
+        Pool &P = *pp;
+        if (!P.timed) continue;
+        err = cudaStreamSynchronize(P.stream);
+        if (err != cudaSuccess) return cuda_error(err, "server: round");
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, P.ev0, P.ev1);
+        gpu_ms = std::max(gpu_ms, ms);  // the codes overlap: the round takes its slowest code
+    }
     // ---- 3. finished frames: gather and copy their outputs
     std::vector<int> nfin(sv->pools.size(), 0);
     for (size_t pi = 0; pi < sv->pools.size(); ++pi) {
@@ -301,18 +325,22 @@ int run_round(lpdec_server *sv) {
         nfin[pi] = nf;
         if (!nf) continue;
         const int n = P.code->n;
-        err = cudaMemcpyAsync(P.d_fin, P.h_fin, (size_t)nf * 4, cudaMemcpyHostToDevice, sv->stream);
+        cudaStream_t st = P.stream;
+        err = cudaMemcpyAsync(P.d_fin, P.h_fin, (size_t)nf * 4, cudaMemcpyHostToDevice, st);
         if (err != cudaSuccess) return cuda_error(err, "server: finished list copy");
-        gather_outputs<<<nf, 128, 0, sv->stream>>>(n, nf, P.d_fin, P.x, P.bits, P.iters, P.cert, P.d_xo, P.d_bo, P.d_io,
-                                                   P.d_co);
-        err = cudaMemcpyAsync(P.h_xo, P.d_xo, (size_t)nf * n * 4, cudaMemcpyDeviceToHost, sv->stream);
-        if (err == cudaSuccess) err = cudaMemcpyAsync(P.h_bo, P.d_bo, (size_t)nf * n, cudaMemcpyDeviceToHost, sv->stream);
-        if (err == cudaSuccess) err = cudaMemcpyAsync(P.h_io, P.d_io, (size_t)nf * 4, cudaMemcpyDeviceToHost, sv->stream);
-        if (err == cudaSuccess) err = cudaMemcpyAsync(P.h_co, P.d_co, (size_t)nf, cudaMemcpyDeviceToHost, sv->stream);
+        gather_outputs<<<nf, 128, 0, st>>>(n, nf, P.d_fin, P.x, P.bits, P.iters, P.cert, P.d_xo, P.d_bo, P.d_io,
+                                           P.d_co);
+        err = cudaMemcpyAsync(P.h_xo, P.d_xo, (size_t)nf * n * 4, cudaMemcpyDeviceToHost, st);
+        if (err == cudaSuccess) err = cudaMemcpyAsync(P.h_bo, P.d_bo, (size_t)nf * n, cudaMemcpyDeviceToHost, st);
+        if (err == cudaSuccess) err = cudaMemcpyAsync(P.h_io, P.d_io, (size_t)nf * 4, cudaMemcpyDeviceToHost, st);
+        if (err == cudaSuccess) err = cudaMemcpyAsync(P.h_co, P.d_co, (size_t)nf, cudaMemcpyDeviceToHost, st);
         if (err != cudaSuccess) return cuda_error(err, "server: output copy");
     }
-    err = cudaStreamSynchronize(sv->stream);
-    if (err != cudaSuccess) return cuda_error(err, "server: output gather");
+    for (size_t pi = 0; pi < sv->pools.size(); ++pi) {
+        if (!nfin[pi]) continue;
+        err = cudaStreamSynchronize(sv->pools[pi]->stream);
+        if (err != cudaSuccess) return cuda_error(err, "server: output gather");
+    }
     // ---- 4. hand results to their requests (under the lock)
     {
         std::lock_guard<std::mutex> lk(sv->mu);
@@ -401,8 +429,6 @@ extern "C" int lpdec_server_create(size_t device_budget_bytes, void *cuda_stream
         return lpdec::cuda_error(err, "lpdec_server_create: cudaGetDevice");
     }
     sv->budget = device_budget_bytes;
-    cudaEventCreate(&sv->ev0);
-    cudaEventCreate(&sv->ev1);
     if (cuda_stream) {
         sv->stream = static_cast<cudaStream_t>(cuda_stream);
     } else {
@@ -561,12 +587,14 @@ extern "C" int lpdec_server_destroy(lpdec_server *sv) {
     if (sv->worker_started) sv->worker.join();  // drains the frames already submitted
     int rc = LPDEC_OK;
     for (auto &pp : sv->pools) {
+        if (pp->stream) cudaStreamSynchronize(pp->stream);
         if (pp->dev && cudaFree(pp->dev) != cudaSuccess) rc = LPDEC_ECUDA;
         if (pp->host && cudaFreeHost(pp->host) != cudaSuccess) rc = LPDEC_ECUDA;
+        if (pp->ev0) cudaEventDestroy(pp->ev0);
+        if (pp->ev1) cudaEventDestroy(pp->ev1);
+        if (pp->stream) cudaStreamDestroy(pp->stream);
     }
     if (sv->own_stream) cudaStreamDestroy(sv->stream);
-    if (sv->ev0) cudaEventDestroy(sv->ev0);
-    if (sv->ev1) cudaEventDestroy(sv->ev1);
     delete sv;
     if (rc) return set_error(rc, "lpdec_server_destroy: freeing device memory failed");
     return LPDEC_OK;
