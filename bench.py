@@ -53,9 +53,14 @@ def parse():
     ap.add_argument("--variants", type=int, default=1, help="also time the other schedules/precisions")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "mixed", "precision", "served"],
+    ap.add_argument("--workload", default="single",
+                    choices=["single", "mixed", "precision", "served", "bsc", "sweep"],
                     help="single: the headline C1056 batch; mixed: three codes in one persistent launch; "
-                         "precision: FP32 / BF16 / FP16 state storage; served: Poisson request stream")
+                         "precision: FP32 / BF16 / FP16 state storage; served: Poisson request stream; "
+                         "bsc: random (3,6) ensemble over the BSC; sweep: eps / mu / rho parameter study")
+    ap.add_argument("--ensemble-codes", type=int, default=10)
+    ap.add_argument("--ensemble-frames", type=int, default=1000, help="frames per code per crossover")
+    ap.add_argument("--sweep-frames", type=int, default=4000)
     ap.add_argument("--served-rate", type=float, default=2e5, help="offered load, frames/s")
     ap.add_argument("--served-requests", type=int, default=200_000)
     ap.add_argument("--served-round", type=int, default=8, help="ADMM iterations per server round")
@@ -504,9 +509,24 @@ def run_served(args):
     st = srv.stats()
     ctr = srv.counters()
     srv.close()
-    for h in handles:
-        h.close()
     info = sum(codes[c].k_design for c in which)
+    # The plain path on the same frame mix: every pool frame decoded as a batch of
+    # its code with one launch per iteration (STREAMED) and with the RESIDENT
+    # schedule, same parameters and early exit.
+    plain = {}
+    for sched in ("streamed", "resident"):
+        pp = lpdec.make_params(mu=MU, rho=RHO, eps=1e-5, max_iter=1000, state="f32", schedule=sched)
+        d_pools = [torch.from_numpy(pl).cuda() for pl in pools]
+        outs = [lpdec.decode(h, dp, pp) for h, dp in zip(handles, d_pools)]
+
+        def run_all():
+            for h, dp, o in zip(handles, d_pools, outs):
+                lpdec.decode(h, dp, pp, out=o)
+
+        ms = _time_call(run_all, 1, 1)
+        bits_pool = sum(codes[c].k_design * POOL for c in range(4))
+        plain[f"per_code_{sched}_batches"] = {"value": bits_pool / (ms / 1000.0), "ms": ms,
+                                              "frames": 4 * POOL}
     line = {
         "workload": "served", "metric": "ADMM-LP served decode stream: sustained info bits/s, p50/p99 latency",
         "unit": UNIT, "value": st["bits_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
@@ -528,8 +548,84 @@ def run_served(args):
         "mean_iters": {names[c]: float(iters[which == c].mean()) for c in range(4)},
         "wer": {names[c]: float(err[which == c].mean()) for c in range(4)},
         "tiles": {names[c]: tiles[c] for c in range(4)},
+        "vs_plain": plain,
     }
+    for h in handles:
+        h.close()
     print(json.dumps(line), flush=True)
+
+
+def run_bsc(args):
+    """Random (3,6) n=1002 ensemble over the BSC: WER, BER, iterations split by outcome, ML lower bound."""
+    import torch
+
+    from paper_1204_0556_gb300 import analysis as A, build, inputs as I, lpdec
+
+    build.build()
+    ens = I.gallager_ensemble(1002, 3, 6, args.ensemble_codes)
+    p = lpdec.make_params(mu=MU, rho=RHO, eps=1e-5, max_iter=1000, state="f32", schedule="resident")
+    rows = []
+    for cp in (0.03, 0.04, 0.05, 0.06, 0.07, 0.08):
+        bits_all, iters_all, llr_all, mlb, frac, ms_tot = [], [], [], 0, 0, 0.0
+        for k, code in enumerate(ens):
+            C = lpdec.Code(code)
+            llr = I.bsc_llr(code, cp, args.ensemble_frames, 7000 + 100 * k + int(cp * 1000))
+            d = torch.from_numpy(llr).cuda()
+            out = lpdec.decode(C, d, p)
+            ms_tot += _time_call(lambda: lpdec.decode(C, d, p, out=out), 1, 0)
+            bits = out["bits"].cpu().numpy()
+            iters = out["iters"].cpu().numpy()
+            mlb += int(A.ml_lower_bound_errors(code, llr, bits).sum())
+            frac += A.pseudocodeword_summary(out["x"].cpu().numpy())["frames_fractional"]
+            bits_all.append(bits)
+            iters_all.append(iters)
+            C.close()
+        e = A.error_rates(np.concatenate(bits_all), np.concatenate(iters_all))
+        F = e["frames"]
+        e.update({"crossover": cp, "ml_lower_bound_wer": mlb / F, "fractional_frames": frac / F,
+                  "frames_per_s": F / (ms_tot / 1000.0)})
+        rows.append(e)
+    print(json.dumps({"workload": "bsc", "codes": f"{args.ensemble_codes} seeded (3,6) Gallager codes, n=1002",
+                      "frames_per_code": args.ensemble_frames, "mu": MU, "rho": RHO, "eps": 1e-5,
+                      "max_iter": 1000, "rows": rows}), flush=True)
+
+
+def run_sweep(args):
+    """Parameter study on a (3,6) n=2640 code: WER, mean iterations and time vs eps, mu and rho."""
+    import torch
+
+    from paper_1204_0556_gb300 import analysis as A, build, inputs as I, lpdec
+
+    build.build()
+    code = I.gallager_code(2640, 3, 6, 5, remove_4cycles=True, name="(3,6) n=2640")
+    C = lpdec.Code(code)
+    F = args.sweep_frames
+    cache = {}
+
+    def point(snr, mu, rho, eps):
+        if snr not in cache:
+            cache[snr] = torch.from_numpy(I.awgn_llr(code, snr, F, 9000 + int(10 * snr))).cuda()
+        d = cache[snr]
+        p = lpdec.make_params(mu=mu, rho=rho, eps=eps, max_iter=1000, state="f32", schedule="resident")
+        out = lpdec.decode(C, d, p)
+        ms = _time_call(lambda: lpdec.decode(C, d, p, out=out), 1, 0)
+        e = A.error_rates(out["bits"].cpu().numpy(), out["iters"].cpu().numpy())
+        return {"snr_db": snr, "mu": mu, "rho": rho, "eps": eps, "wer": e["wer"], "iters_mean": e["iters_mean"],
+                "ms_per_frame": ms / F}
+
+    rows = []
+    for mu in (1.0, 5.0, 7.0):  # WER vs the stopping tolerance (no over-relaxation)
+        for bits_tol in (10, 14, 17, 20):
+            rows.append(point(2.2, mu, 1.0, 2.0 ** -bits_tol))
+    for snr in (1.9, 2.2, 2.5):  # WER and time vs mu
+        for mu in (1.0, 2.0, 3.0, 5.0, 7.0, 10.0):
+            rows.append(point(snr, mu, 1.0, 1e-5))
+    for mu in (1.0, 3.0, 5.0, 7.0):  # time vs over-relaxation
+        for rho in (1.0, 1.3, 1.6, 1.9):
+            rows.append(point(2.8, mu, rho, 1e-5))
+    C.close()
+    print(json.dumps({"workload": "sweep", "code": "(3,6) Gallager n=2640 seed 5, 4-cycle free",
+                      "frames_per_point": F, "max_iter": 1000, "rows": rows}), flush=True)
 
 
 def main():
@@ -546,6 +642,12 @@ def main():
         return
     if args.workload == "served":
         run_served(args)
+        return
+    if args.workload == "bsc":
+        run_bsc(args)
+        return
+    if args.workload == "sweep":
+        run_sweep(args)
         return
 
     import torch

@@ -47,6 +47,7 @@ __all__ = [
     "sigma2_for",
     "benchmark_code",
     "count_4cycles",
+    "gallager_ensemble",
 ]
 
 
@@ -344,3 +345,11 @@ _BENCH = {
 def benchmark_code(name: str, seed: int = 0) -> Code:
     """One of the benchmark code shapes, built from ``seed``."""
     return _BENCH[name](seed)
+
+
+def gallager_ensemble(n: int, dv: int, dc: int, count: int, seed0: int = 1000) -> list[Code]:
+    """``count`` seeded members of the regular (dv, dc) Gallager ensemble (seeds
+    seed0, seed0+1, ...).  Rows never repeat a column, so no member has parallel
+    edges; 4-cycles are kept, as in the random-ensemble experiment of Section 5.1."""
+    return [gallager_code(n, dv, dc, seed0 + k, remove_4cycles=False, name=f"ens({dv},{dc}) n={n} #{k}")
+            for k in range(count)]

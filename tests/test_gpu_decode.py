@@ -287,3 +287,18 @@ def test_autotune_keeps_results(gpu, c1056):
             gpu.lpdec_set_tile(C.handle, 0, 48, 1)  # not a whole number of warps
     finally:
         C.close()
+
+
+@pytest.mark.parametrize("mu,rho", [(1.0, 1.0), (7.0, 1.5), (3.0, 1.99)])
+def test_other_penalties_and_relaxations(gpu, oracle_mod, c96, mu, rho):
+    llr = I.awgn_llr(c96, 2.0, 40, 21)
+    kw = dict(mu=mu, rho=rho, eps=0.0, max_iter=150)
+    assert_parity(c96, gpu_decode(gpu, c96, llr, **kw), oracle_decode(oracle_mod, c96, llr, **kw), 1e-4)
+
+
+def test_bsc_ensemble_member(gpu, oracle_mod):
+    """BSC LLRs (two magnitudes only, many ties in v) on a random (3,6) n=1002 code."""
+    code = I.gallager_ensemble(1002, 3, 6, 1)[0]
+    llr = I.bsc_llr(code, 0.05, 60, 31)
+    kw = dict(mu=MU, rho=RHO, eps=0.0, max_iter=200)
+    assert_parity(code, gpu_decode(gpu, code, llr, **kw), oracle_decode(oracle_mod, code, llr, **kw), 1e-4)
