@@ -67,6 +67,7 @@ extern "C" {
 
 typedef struct lpdec_code lpdec_code;     /* opaque: a parity-check matrix resident on one GPU */
 typedef struct lpdec_server lpdec_server; /* opaque: a continuous-batching decode server */
+typedef struct lpdec_mixed_plan lpdec_mixed_plan; /* opaque: a prepared mixed-code launch */
 
 /* Decoder parameters (Algorithm 1 caption; Section 5.1 for the paper's defaults). */
 typedef struct lpdec_params {
@@ -202,6 +203,25 @@ LPDEC_API int lpdec_decode_mixed(const lpdec_code *const *codes, int32_t n_codes
                                  const int32_t *frame_code, const float *llr, const lpdec_params *params,
                                  float *x_out, uint8_t *bits_out, int32_t *iters_out, uint8_t *cert_out,
                                  void *cuda_stream);
+
+/*
+ * A prepared mixed-code decode, for batches whose composition repeats (the
+ * same codes in the same frame order, new LLRs each time).
+ *   lpdec_mixed_plan_create: validates like lpdec_decode_mixed, chooses the
+ *       tiles, and copies the per-frame offsets and per-code frame lists to
+ *       device memory it owns (synchronous; params are fixed for the plan).
+ *   lpdec_mixed_plan_decode: queues one counter reset and ONE persistent kernel
+ *       launch on cuda_stream, with buffers laid out as in lpdec_decode_mixed.
+ *       It touches no host memory and allocates nothing, so it can be captured
+ *       into a CUDA graph and replayed.  A plan serves one decode at a time.
+ *   lpdec_mixed_plan_destroy: frees the plan (no decode may be in flight).
+ */
+LPDEC_API int lpdec_mixed_plan_create(const lpdec_code *const *codes, int32_t n_codes, int32_t n_frames,
+                                      const int32_t *frame_code, const lpdec_params *params,
+                                      lpdec_mixed_plan **out);
+LPDEC_API int lpdec_mixed_plan_decode(lpdec_mixed_plan *plan, const float *llr, float *x_out, uint8_t *bits_out,
+                                      int32_t *iters_out, uint8_t *cert_out, void *cuda_stream);
+LPDEC_API int lpdec_mixed_plan_destroy(lpdec_mixed_plan *plan);
 
 /*
  * As lpdec_decode, for callers that must not allocate device memory while they

@@ -132,44 +132,60 @@ int kind_of(const lpdec_code *c) {
     }
 }
 
-}  // namespace
-}  // namespace lpdec
+// Everything a mixed launch needs except the batch buffers: argument block,
+// launch shape, and the host copies of the per-frame offsets and per-code
+// frame lists.
+struct MixedSetup {
+    MixedArgs a;
+    int grid = 0, block = 0;
+    size_t smem = 0;
+    const void *fn = nullptr;
+    int n_frames = 0;
+    std::vector<long long> offset;
+    std::vector<int> flat;
+    std::vector<int> list_start;
+    long long *d_offset = nullptr;  // device copies, set by mixed_bind
+    int *d_flat = nullptr;
+    size_t work_bytes() const {
+        return 256 + ((offset.size() * 8 + 255) & ~(size_t)255) + flat.size() * 4;
+    }
+};
 
-extern "C" int lpdec_decode_mixed(const lpdec_code *const *codes, int32_t n_codes, int32_t n_frames,
-                                  const int32_t *frame_code, const float *llr, const lpdec_params *p,
-                                  float *x_out, uint8_t *bits_out, int32_t *iters_out, uint8_t *cert_out,
-                                  void *cuda_stream) {
-    using namespace lpdec;
+int mixed_setup(const char *who, const lpdec_code *const *codes, int32_t n_codes, int32_t n_frames,
+                const int32_t *frame_code, const lpdec_params *p, MixedSetup &S) {
     if (!codes || n_codes < 1 || n_codes > kMaxMixedCodes)
-        return set_error(LPDEC_EINVAL, "lpdec_decode_mixed: n_codes=%d must be in [1, %d]", n_codes, kMaxMixedCodes);
-    if (n_frames < 0) return set_error(LPDEC_EINVAL, "lpdec_decode_mixed: n_frames=%d < 0", n_frames);
+        return set_error(LPDEC_EINVAL, "%s: n_codes=%d must be in [1, %d]", who, n_codes, kMaxMixedCodes);
+    if (n_frames < 0) return set_error(LPDEC_EINVAL, "%s: n_frames=%d < 0", who, n_frames);
     int rc = validate_params(p);
     if (rc) return rc;
-    if (p->schedule == LPDEC_SCHED_STREAMED)
-        return set_error(LPDEC_EINVAL, "lpdec_decode_mixed: runs the RESIDENT schedule only");
+    if (p->schedule == LPDEC_SCHED_STREAMED) return set_error(LPDEC_EINVAL, "%s: runs the RESIDENT schedule only", who);
     for (int c = 0; c < n_codes; ++c)
-        if (!codes[c]) return set_error(LPDEC_EINVAL, "lpdec_decode_mixed: codes[%d] is NULL", c);
-    if (n_frames == 0) return LPDEC_OK;
-    if (!frame_code || !llr || !x_out)
-        return set_error(LPDEC_EINVAL, "lpdec_decode_mixed: frame_code, llr and x_out must not be NULL");
+        if (!codes[c]) return set_error(LPDEC_EINVAL, "%s: codes[%d] is NULL", who, c);
+    if (n_frames > 0 && !frame_code) return set_error(LPDEC_EINVAL, "%s: frame_code must not be NULL", who);
     const int dev = codes[0]->device;
     for (int c = 1; c < n_codes; ++c)
-        if (codes[c]->device != dev) return set_error(LPDEC_EINVAL, "lpdec_decode_mixed: codes on different devices");
+        if (codes[c]->device != dev) return set_error(LPDEC_EINVAL, "%s: codes on different devices", who);
 
     // per-frame offsets and per-code frame lists
-    std::vector<long long> offset((size_t)n_frames);
+    S.n_frames = n_frames;
+    S.offset.assign((size_t)n_frames, 0);
     std::vector<std::vector<int>> lists((size_t)n_codes);
     long long off = 0;
     for (int f = 0; f < n_frames; ++f) {
         const int c = frame_code[f];
-        if (c < 0 || c >= n_codes)
-            return set_error(LPDEC_EINVAL, "lpdec_decode_mixed: frame_code[%d]=%d out of range", f, c);
-        offset[f] = off;
+        if (c < 0 || c >= n_codes) return set_error(LPDEC_EINVAL, "%s: frame_code[%d]=%d out of range", who, f, c);
+        S.offset[f] = off;
         off += codes[c]->n;
         lists[c].push_back(f);
     }
+    S.flat.clear();
+    S.list_start.assign((size_t)n_codes, 0);
+    for (int c = 0; c < n_codes; ++c) {
+        S.list_start[c] = (int)S.flat.size();
+        S.flat.insert(S.flat.end(), lists[c].begin(), lists[c].end());
+    }
 
-    MixedArgs a;
+    MixedArgs &a = S.a;
     std::memset(&a, 0, sizeof(a));
     a.n_codes = n_codes;
     int block = 32;
@@ -181,11 +197,11 @@ extern "C" int lpdec_decode_mixed(const lpdec_code *const *codes, int32_t n_code
         Tile tile = cc->tuned[p->state_dtype].valid ? cc->tuned[p->state_dtype] : default_tile(cc, p->state_dtype);
         if (tile.group_threads > kMixedMaxThreads) tile = default_tile(cc, p->state_dtype, kMixedMaxThreads);
         if (tile.group_threads > kMixedMaxThreads)
-            return set_error(LPDEC_EINVAL, "lpdec_decode_mixed: code %d needs %d threads per frame (limit %d)", c,
+            return set_error(LPDEC_EINVAL, "%s: code %d needs %d threads per frame (limit %d)", who, c,
                              tile.group_threads, kMixedMaxThreads);
         const SliceLayout L = slice_layout(cc, p->state_dtype, tile.group_threads);
         if ((int)L.bytes > cap)
-            return set_error(LPDEC_EINVAL, "lpdec_decode_mixed: code %d's frame state does not fit in shared memory", c);
+            return set_error(LPDEC_EINVAL, "%s: code %d's frame state does not fit in shared memory", who, c);
         layouts[c] = L;
         MixedCode &mc = a.code[c];
         mc.view = make_view(cc);
@@ -211,58 +227,133 @@ extern "C" int lpdec_decode_mixed(const lpdec_code *const *codes, int32_t n_code
         mc.groups = std::max(1, g);
         block = std::max(block, mc.groups * mc.group_threads);
     }
-    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
-    const void *fn = mixed_fn(p->state_dtype);
-    cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return cuda_error(err, "lpdec_decode_mixed: cudaFuncSetAttribute");
+    S.fn = mixed_fn(p->state_dtype);
+    cudaError_t err = cudaFuncSetAttribute(S.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return cuda_error(err, "mixed decode: cudaFuncSetAttribute");
     int bps = 0;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, block, smem);
-    if (err != cudaSuccess) return cuda_error(err, "lpdec_decode_mixed: occupancy");
-    if (bps < 1) return set_error(LPDEC_EINVAL, "lpdec_decode_mixed: tile does not fit on an SM");
-    const int grid = bps * device_sm_count(dev);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, S.fn, block, smem);
+    if (err != cudaSuccess) return cuda_error(err, "mixed decode: occupancy");
+    if (bps < 1) return set_error(LPDEC_EINVAL, "%s: tile does not fit on an SM", who);
+    S.grid = bps * device_sm_count(dev);
+    S.block = block;
+    S.smem = smem;
     // home codes: CTAs split in proportion to each code's edge work
     double total = 0.0;
     for (int c = 0; c < n_codes; ++c) total += (double)a.code[c].n_frames * codes[c]->E;
-    int acc = 0;
     double run = 0.0;
     for (int c = 0; c < n_codes; ++c) {
         run += (double)a.code[c].n_frames * codes[c]->E;
-        acc = (int)std::lround(grid * (total > 0 ? run / total : 1.0));
-        a.home_end[c] = c == n_codes - 1 ? grid : acc;
+        const int acc = (int)std::lround(S.grid * (total > 0 ? run / total : 1.0));
+        a.home_end[c] = c == n_codes - 1 ? S.grid : acc;
     }
+    return LPDEC_OK;
+}
 
-    // workspace: queues, offsets, frame lists
-    const size_t qb = 256, ob = ((size_t)n_frames * 8 + 255) & ~(size_t)255, lb = (size_t)n_frames * 4;
+// Point the argument block at a device workspace laid out as
+// [256 B queue counters | offsets | frame lists].
+void mixed_bind(MixedSetup &S, char *work, const float *llr, float *x_out, uint8_t *bits_out, int32_t *iters_out,
+                uint8_t *cert_out) {
+    const size_t ob = (S.offset.size() * 8 + 255) & ~(size_t)255;
+    S.a.queues = reinterpret_cast<int *>(work);
+    S.d_offset = reinterpret_cast<long long *>(work + 256);
+    S.d_flat = reinterpret_cast<int *>(work + 256 + ob);
+    S.a.offset = S.d_offset;
+    for (int c = 0; c < S.a.n_codes; ++c) S.a.code[c].frames = S.d_flat + S.list_start[c];
+    S.a.llr = llr;
+    S.a.x_out = x_out;
+    S.a.bits_out = bits_out;
+    S.a.iters_out = iters_out;
+    S.a.cert_out = cert_out;
+}
+
+// Queue the launch: zero the counters, run the kernel.  No host memory is
+// touched and nothing is allocated, so this can be captured in a CUDA graph.
+int mixed_launch(MixedSetup &S, cudaStream_t stream) {
+    cudaError_t err = cudaMemsetAsync(S.a.queues, 0, 256, stream);
+    if (err != cudaSuccess) return cuda_error(err, "mixed decode: cudaMemsetAsync");
+    void *args[] = {&S.a};
+    err = cudaLaunchKernel(S.fn, dim3(S.grid), dim3(S.block), args, S.smem, stream);
+    if (err != cudaSuccess) return cuda_error(err, "mixed decode: launch");
+    return LPDEC_OK;
+}
+
+}  // namespace
+}  // namespace lpdec
+
+struct lpdec_mixed_plan {
+    lpdec::MixedSetup setup;
+    void *work = nullptr;
+};
+
+extern "C" int lpdec_decode_mixed(const lpdec_code *const *codes, int32_t n_codes, int32_t n_frames,
+                                  const int32_t *frame_code, const float *llr, const lpdec_params *p,
+                                  float *x_out, uint8_t *bits_out, int32_t *iters_out, uint8_t *cert_out,
+                                  void *cuda_stream) {
+    using namespace lpdec;
+    MixedSetup S;
+    int rc = mixed_setup("lpdec_decode_mixed", codes, n_codes, n_frames, frame_code, p, S);
+    if (rc) return rc;
+    if (n_frames == 0) return LPDEC_OK;
+    if (!llr || !x_out) return set_error(LPDEC_EINVAL, "lpdec_decode_mixed: llr and x_out must not be NULL");
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
     char *work = nullptr;
-    err = cudaMallocAsync(reinterpret_cast<void **>(&work), qb + ob + lb, stream);
+    cudaError_t err = cudaMallocAsync(reinterpret_cast<void **>(&work), S.work_bytes(), stream);
     if (err != cudaSuccess) return cuda_error(err, "lpdec_decode_mixed: cudaMallocAsync");
-    a.queues = reinterpret_cast<int *>(work);
-    a.offset = reinterpret_cast<const long long *>(work + qb);
-    int *flat = reinterpret_cast<int *>(work + qb + ob);
-    std::vector<int> flat_h;
-    flat_h.reserve((size_t)n_frames);
-    for (int c = 0; c < n_codes; ++c) {
-        a.code[c].frames = flat + flat_h.size();
-        flat_h.insert(flat_h.end(), lists[c].begin(), lists[c].end());
-    }
-    a.llr = llr;
-    a.x_out = x_out;
-    a.bits_out = bits_out;
-    a.iters_out = iters_out;
-    a.cert_out = cert_out;
-    rc = LPDEC_OK;
-    err = cudaMemsetAsync(work, 0, qb, stream);
+    mixed_bind(S, work, llr, x_out, bits_out, iters_out, cert_out);
+    err = cudaMemcpyAsync(S.d_offset, S.offset.data(), S.offset.size() * 8, cudaMemcpyHostToDevice, stream);
     if (err == cudaSuccess)
-        err = cudaMemcpyAsync(work + qb, offset.data(), (size_t)n_frames * 8, cudaMemcpyHostToDevice, stream);
-    if (err == cudaSuccess)
-        err = cudaMemcpyAsync(flat, flat_h.data(), (size_t)n_frames * 4, cudaMemcpyHostToDevice, stream);
-    if (err != cudaSuccess) rc = cuda_error(err, "lpdec_decode_mixed: workspace upload");
-    if (!rc) {
-        void *args[] = {&a};
-        err = cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, stream);
-        if (err != cudaSuccess) rc = cuda_error(err, "lpdec_decode_mixed: launch");
-    }
+        err = cudaMemcpyAsync(S.d_flat, S.flat.data(), S.flat.size() * 4, cudaMemcpyHostToDevice, stream);
+    rc = err != cudaSuccess ? cuda_error(err, "lpdec_decode_mixed: workspace upload") : mixed_launch(S, stream);
     err = cudaFreeAsync(work, stream);
     if (!rc && err != cudaSuccess) rc = cuda_error(err, "lpdec_decode_mixed: cudaFreeAsync");
     return rc;
+}
+
+extern "C" int lpdec_mixed_plan_create(const lpdec_code *const *codes, int32_t n_codes, int32_t n_frames,
+                                       const int32_t *frame_code, const lpdec_params *p, lpdec_mixed_plan **out) {
+    using namespace lpdec;
+    if (!out) return set_error(LPDEC_EINVAL, "lpdec_mixed_plan_create: out is NULL");
+    if (n_frames < 1) return set_error(LPDEC_EINVAL, "lpdec_mixed_plan_create: n_frames must be >= 1");
+    auto *plan = new (std::nothrow) lpdec_mixed_plan();
+    if (!plan) return set_error(LPDEC_ENOMEM, "lpdec_mixed_plan_create: host allocation failed");
+    int rc = mixed_setup("lpdec_mixed_plan_create", codes, n_codes, n_frames, frame_code, p, plan->setup);
+    if (rc) {
+        delete plan;
+        return rc;
+    }
+    MixedSetup &S = plan->setup;
+    cudaError_t err = cudaMalloc(&plan->work, S.work_bytes());
+    if (err != cudaSuccess) {
+        delete plan;
+        return cuda_error(err, "lpdec_mixed_plan_create: cudaMalloc");
+    }
+    char *w = static_cast<char *>(plan->work);
+    mixed_bind(S, w, nullptr, nullptr, nullptr, nullptr, nullptr);
+    err = cudaMemcpy(S.d_offset, S.offset.data(), S.offset.size() * 8, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemcpy(S.d_flat, S.flat.data(), S.flat.size() * 4, cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) {
+        cudaFree(plan->work);
+        delete plan;
+        return cuda_error(err, "lpdec_mixed_plan_create: upload");
+    }
+    *out = plan;
+    return LPDEC_OK;
+}
+
+extern "C" int lpdec_mixed_plan_decode(lpdec_mixed_plan *plan, const float *llr, float *x_out, uint8_t *bits_out,
+                                       int32_t *iters_out, uint8_t *cert_out, void *cuda_stream) {
+    using namespace lpdec;
+    if (!plan) return set_error(LPDEC_EINVAL, "lpdec_mixed_plan_decode: plan is NULL");
+    if (!llr || !x_out) return set_error(LPDEC_EINVAL, "lpdec_mixed_plan_decode: llr and x_out must not be NULL");
+    MixedSetup &S = plan->setup;
+    mixed_bind(S, static_cast<char *>(plan->work), llr, x_out, bits_out, iters_out, cert_out);
+    return mixed_launch(S, static_cast<cudaStream_t>(cuda_stream));
+}
+
+extern "C" int lpdec_mixed_plan_destroy(lpdec_mixed_plan *plan) {
+    if (!plan) return lpdec::set_error(LPDEC_EINVAL, "lpdec_mixed_plan_destroy: plan is NULL");
+    const cudaError_t err = cudaFree(plan->work);
+    delete plan;
+    if (err != cudaSuccess) return lpdec::cuda_error(err, "lpdec_mixed_plan_destroy: cudaFree");
+    return LPDEC_OK;
 }

@@ -40,6 +40,7 @@ EXPORTED = [
     "lpdec_decode_mixed",
     "lpdec_server_create", "lpdec_server_add_code", "lpdec_server_submit", "lpdec_server_poll",
     "lpdec_server_stats", "lpdec_server_destroy", "lpdec_autotune", "lpdec_set_tile", "lpdec_server_counters",
+    "lpdec_mixed_plan_create", "lpdec_mixed_plan_decode", "lpdec_mixed_plan_destroy",
 ]
 
 
@@ -108,6 +109,10 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
             "lpdec_server_counters": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), dp, dp]),
             "lpdec_autotune": (ctypes.c_int, [_vp, P, _i32, _vp, _vp, _i32p, _i32p, dp]),
             "lpdec_set_tile": (ctypes.c_int, [_vp, _i32, _i32, _i32]),
+            "lpdec_mixed_plan_create": (ctypes.c_int, [ctypes.POINTER(_vp), _i32, _i32, _i32p, P,
+                                                       ctypes.POINTER(_vp)]),
+            "lpdec_mixed_plan_decode": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+            "lpdec_mixed_plan_destroy": (ctypes.c_int, [_vp]),
         })
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -242,6 +247,23 @@ def lpdec_autotune(handle: int, params, n_frames: int, llr_ptr: int, stream_ptr:
 
 def lpdec_set_tile(handle: int, state_dtype: int, group_threads: int, groups: int) -> None:
     _check(load().lpdec_set_tile(handle, state_dtype, group_threads, groups))
+
+
+def lpdec_mixed_plan_create(handles, frame_code, params) -> int:
+    arr = (_vp * len(handles))(*handles)
+    fc = _i32arr(frame_code)
+    out = _vp()
+    _check(load().lpdec_mixed_plan_create(arr, len(handles), len(fc), fc.ctypes.data_as(_i32p), ctypes.byref(params),
+                                          ctypes.byref(out)))
+    return out.value
+
+
+def lpdec_mixed_plan_decode(plan, llr_ptr, x_ptr, bits_ptr, iters_ptr, cert_ptr, stream_ptr) -> None:
+    _check(load().lpdec_mixed_plan_decode(plan, llr_ptr, x_ptr, bits_ptr, iters_ptr, cert_ptr, stream_ptr))
+
+
+def lpdec_mixed_plan_destroy(plan) -> None:
+    _check(load().lpdec_mixed_plan_destroy(plan))
 
 
 def lpdec_project(d, count, v_ptr, z_ptr, stream_ptr) -> None:
