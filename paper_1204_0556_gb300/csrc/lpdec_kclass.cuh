@@ -1,6 +1,8 @@
 // Instantiates the decode and projection kernels of one degree class.
 // Each lpdec_kD.cu defines LPDEC_D and includes this file, so the classes
 // compile as separate translation units (in parallel).
+#include <atomic>
+
 #include "lpdec_internal.h"
 
 #ifndef LPDEC_D
@@ -51,10 +53,28 @@ cudaError_t launch_dv(int dtype, const DecodeArgs &a, const LaunchCfg &lc) {
 }
 }  // namespace
 
+// Largest dynamic shared memory already granted to each kernel of this class
+// ([dtype][regular form]); the attribute is set only when a launch needs more,
+// so decodes in a steady state (and under CUDA-graph capture) make no
+// attribute calls.  Per device: a kernel attribute is per device.
+static std::atomic<int> g_smem_granted[64][3][2];
+
 cudaError_t LPDEC_CAT(prepare_decode_, LPDEC_D)(int dtype, int reg_dv, size_t smem) {
     const void *fn = decode_fn_for(dtype, reg_dv);
     if (!fn) return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    if (dev < 0 || dev >= 64) return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    std::atomic<int> &granted = g_smem_granted[dev][dtype][(kRegDV > 0 && reg_dv == kRegDV) ? 1 : 0];
+    if ((int)smem <= granted.load()) return cudaSuccess;
+    err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err == cudaSuccess) {
+        int cur = granted.load();
+        while ((int)smem > cur && !granted.compare_exchange_weak(cur, (int)smem)) {
+        }
+    }
+    return err;
 }
 
 cudaError_t LPDEC_CAT(occupancy_decode_, LPDEC_D)(int dtype, int reg_dv, int block, size_t smem,
