@@ -1,4 +1,5 @@
-"""FP64 CPU oracle for ADMM LP decoding -- TEST INFRASTRUCTURE ONLY.
+"""FP64 CPU oracle for ADMM LP decoding (and the appendix's dual subgradient
+decoder) -- TEST INFRASTRUCTURE ONLY.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The product library (``liblpdec``)
@@ -53,8 +54,12 @@ def _load():
             ctypes.c_int, ctypes.c_int, i32p, i32p, ctypes.c_int, ctypes.c_int, dp,
             ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
             dp, u8p, i32p, u8p, u8p]
+        lib.oracle_lp_max.argtypes = [ctypes.c_int, dp, dp]
+        lib.oracle_decode_dual.argtypes = [
+            ctypes.c_int, ctypes.c_int, i32p, i32p, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, ctypes.c_int,
+            dp, u8p, i32p, u8p]
         for f in (lib.oracle_project, lib.oracle_project_bisect, lib.oracle_project_many,
-                  lib.oracle_decode):
+                  lib.oracle_decode, lib.oracle_lp_max, lib.oracle_decode_dual):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -85,6 +90,45 @@ def project_many(v: np.ndarray, bisect: bool = False) -> np.ndarray:
                                1 if bisect else 0) != 0:
         raise ValueError("degree out of range")
     return z
+
+
+def lp_max(c) -> np.ndarray:
+    """argmax_{z in PP_d} c^T z (Algorithm 3 of the appendix)."""
+    lib = _load()
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    z = np.empty_like(c)
+    if lib.oracle_lp_max(len(c), _ptr(c, ctypes.c_double), _ptr(z, ctypes.c_double)) != 0:
+        raise ValueError("degree out of range")
+    return z
+
+
+def decode_dual(row_ptr, col_idx, n: int, gamma, mu: float = 1.0, max_iter: int = 1000,
+                threads: int | None = None) -> dict:
+    """Dual subgradient ascent of the appendix on every frame of ``gamma``."""
+    lib = _load()
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+    gamma = np.ascontiguousarray(np.atleast_2d(gamma), dtype=np.float64)
+    F = gamma.shape[0]
+    m = len(row_ptr) - 1
+    x = np.zeros((F, n), dtype=np.float64)
+    bits = np.zeros((F, n), dtype=np.uint8)
+    iters = np.zeros(F, dtype=np.int32)
+    cert = np.zeros(F, dtype=np.uint8)
+    threads = max(1, min(threads or default_threads(), F))
+
+    def run(lo: int, hi: int) -> int:
+        return lib.oracle_decode_dual(
+            n, m, _ptr(row_ptr, ctypes.c_int32), _ptr(col_idx, ctypes.c_int32), lo, hi,
+            _ptr(gamma, ctypes.c_double), mu, max_iter, _ptr(x, ctypes.c_double), _ptr(bits, ctypes.c_uint8),
+            _ptr(iters, ctypes.c_int32), _ptr(cert, ctypes.c_uint8))
+
+    edges = np.linspace(0, F, threads + 1).astype(int)
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        rc = list(ex.map(lambda t: run(int(edges[t]), int(edges[t + 1])), range(threads)))
+    if any(rc):
+        raise ValueError("oracle_decode_dual rejected its arguments")
+    return {"x": x, "bits": bits, "iters": iters, "cert": cert}
 
 
 def default_threads() -> int:

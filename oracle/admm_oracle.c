@@ -288,3 +288,83 @@ int oracle_decode(int n, int m, const int32_t *row_ptr, const int32_t *col_idx,
     free(z); free(lam); free(acc); free(deg); free(x);
     return 0;
 }
+
+/*
+ * Appendix, Algorithm 3: maximize c^T z over the parity polytope PP_d.  The
+ * optimum is an even-weight vertex.  Let r be the number of positive c_i.
+ * r even: z = [c > 0].  r odd: either drop the smallest positive entry i_p or
+ * add the largest non-positive entry i_n, whichever costs less; that is, add
+ * i_n when c_{i_p} + c_{i_n} > 0 (the printed comparison is read this way, see
+ * the design notes), else drop i_p.  Ties pick the lowest index.
+ */
+int oracle_lp_max(int d, const double *c, double *z)
+{
+    if (d < 1 || d > ORACLE_MAX_D) return -1;
+    int r = 0, ip = -1, in = -1;
+    for (int k = 0; k < d; ++k) {
+        z[k] = c[k] > 0.0 ? 1.0 : 0.0;
+        if (c[k] > 0.0) {
+            ++r;
+            if (ip < 0 || c[k] < c[ip]) ip = k;
+        } else if (in < 0 || c[k] > c[in]) {
+            in = k;
+        }
+    }
+    if (r % 2 == 0) return 0;
+    if (in >= 0 && c[ip] + c[in] > 0.0) z[in] = 1.0;
+    else z[ip] = 0.0;
+    return 0;
+}
+
+/*
+ * Appendix: dual subgradient ascent on the un-augmented Lagrangian
+ * L_0 = gamma^T x + sum_j lambda_j^T (P_j x - z_j), for frames [f_lo, f_hi):
+ *   x_i = [ -gamma_i - sum_{j in N_v(i)} lambda_j^(i) > 0 ]   (Heaviside)
+ *   z_j = argmax_{z in PP_d} lambda_j^T z                      (Algorithm 3)
+ *   lambda_j += mu (P_j x - z_j)
+ * both updates taken from the previous lambda.  The method stops when the
+ * subgradient P_j x - z_j vanishes for every j (then lambda is dual optimal and
+ * x an integral LP optimum: the output is certified), else after max_iter.
+ */
+int oracle_decode_dual(int n, int m, const int32_t *row_ptr, const int32_t *col_idx, int f_lo, int f_hi,
+                       const double *gamma, double mu, int max_iter, double *x_out, uint8_t *bits_out,
+                       int32_t *iters_out, uint8_t *cert_out)
+{
+    if (n <= 0 || m <= 0 || mu <= 0.0 || max_iter < 1) return -1;
+    const int E = row_ptr[m];
+    double *lam = (double *)malloc(sizeof(double) * (size_t)E);
+    double *acc = (double *)malloc(sizeof(double) * (size_t)n);
+    double *x = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!lam || !acc || !x) { free(lam); free(acc); free(x); return -1; }
+    for (int f = f_lo; f < f_hi; ++f) {
+        const double *g = gamma + (size_t)f * (size_t)n;
+        for (int e = 0; e < E; ++e) lam[e] = 0.0;
+        int k = 0, done = 0;
+        while (k < max_iter && !done) {
+            for (int i = 0; i < n; ++i) acc[i] = 0.0;
+            for (int e = 0; e < E; ++e) acc[col_idx[e]] += lam[e];
+            for (int i = 0; i < n; ++i) x[i] = (-g[i] - acc[i] > 0.0) ? 1.0 : 0.0;
+            int mismatches = 0;
+            for (int j = 0; j < m; ++j) {
+                const int e0 = row_ptr[j], d = row_ptr[j + 1] - e0;
+                double zj[ORACLE_MAX_D];
+                oracle_lp_max(d, lam + e0, zj);
+                for (int t = 0; t < d; ++t) {
+                    const double s = x[col_idx[e0 + t]] - zj[t];
+                    if (s != 0.0) ++mismatches;
+                    lam[e0 + t] += mu * s;
+                }
+            }
+            ++k;
+            done = mismatches == 0;
+        }
+        for (int i = 0; i < n; ++i) {
+            x_out[(size_t)f * n + i] = x[i];
+            bits_out[(size_t)f * n + i] = x[i] > 0.5 ? 1 : 0;
+        }
+        iters_out[f] = k;
+        cert_out[f] = (uint8_t)done;
+    }
+    free(lam); free(acc); free(x);
+    return 0;
+}
