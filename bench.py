@@ -48,19 +48,22 @@ def parse():
                     help="code of the single-code workload (the headline is C1056)")
     ap.add_argument("--iters", type=int, default=300, help="fixed ADMM iterations of the single-code workload")
     ap.add_argument("--no-autotune", action="store_true", help="use the library's default tile")
+    ap.add_argument("--tile", default="", help="GROUP_THREADS,GROUPS: set the single-code tile instead of autotuning")
     ap.add_argument("--schedule", default="resident", choices=["resident", "streamed", "auto"])
     ap.add_argument("--state", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--variants", type=int, default=1, help="also time the other schedules/precisions")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="single",
-                    choices=["single", "mixed", "precision", "served", "bsc", "sweep"],
+                    choices=["single", "mixed", "precision", "served", "bsc", "sweep", "dual"],
                     help="single: the headline C1056 batch; mixed: three codes in one persistent launch; "
                          "precision: FP32 / BF16 / FP16 state storage; served: Poisson request stream; "
-                         "bsc: random (3,6) ensemble over the BSC; sweep: eps / mu / rho parameter study")
+                         "bsc: random (3,6) ensemble over the BSC; sweep: eps / mu / rho parameter study; "
+                         "dual: dual subgradient decoder (appendix) against ADMM on the same frames")
     ap.add_argument("--ensemble-codes", type=int, default=10)
     ap.add_argument("--ensemble-frames", type=int, default=1000, help="frames per code per crossover")
     ap.add_argument("--sweep-frames", type=int, default=4000)
+    ap.add_argument("--dual-frames", type=int, default=10_000, help="frames per Eb/N0 point of the dual workload")
     ap.add_argument("--served-rate", type=float, default=2e5, help="offered load, frames/s")
     ap.add_argument("--served-requests", type=int, default=200_000)
     ap.add_argument("--served-round", type=int, default=8, help="ADMM iterations per server round")
@@ -153,9 +156,9 @@ def algorithmic_ops_per_frame_iter(code) -> int:
 KERNEL_SOURCES = ("lpdec_device.cuh", "lpdec_kclass.cuh", "lpdec_internal.h")
 MEASURED_TRAFFIC = {
     # "code/schedule": (source hash, bytes per frame per launch, capture)
-    "C1056/resident": ("cbf0bc36e1fe37e2", (33_849_088 + 1_634_560) / 8000,
+    "C1056/resident": ("d32fd46792611e22", (33_850_624 + 1_739_264) / 8000,
                  "profiles/decode_kernel_resident_C1056_small.md: 8000 frames x 300 iterations in one launch"),
-    "C1056/streamed": ("cbf0bc36e1fe37e2", (236_719_872 + 141_154_304) / 8000,
+    "C1056/streamed": ("d32fd46792611e22", (236_679_936 + 141_560_320) / 8000,
                  "profiles/decode_kernel_streamed_C1056_small.md: one iteration of 8000 frames per launch"),
 }
 
@@ -628,6 +631,55 @@ def run_sweep(args):
                       "frames_per_point": F, "max_iter": 1000, "rows": rows}), flush=True)
 
 
+def run_dual(args):
+    """Dual subgradient ascent (appendix) against ADMM (Algorithm 1, early exit)
+    on the same frames: throughput, iterations, WER and certificates, per code,
+    Eb/N0 and dual step size; plus a tile sweep of the dual kernel."""
+    import torch
+
+    from paper_1204_0556_gb300 import analysis as A, build, inputs as I, lpdec
+
+    build.build()
+    F = args.dual_frames
+    rows, tiles = [], []
+    for name, snrs in (("C1056", (3.0, 3.5, 4.0)), ("C2640", (3.0, 3.5))):
+        code = I.benchmark_code(name, CODE_SEEDS[name])
+        C = lpdec.Code(code)
+        k_info = code.n - code.m
+        if name == "C1056":
+            d = torch.from_numpy(I.awgn_llr(code, 3.5, F, 9100)).cuda()
+            for gt, g in ((64, 15), (96, 10), (128, 8), (192, 5), (256, 4), (128, 4), (192, 2), (32, 15)):
+                lpdec.lpdec_dual_set_tile(C.handle, gt, g)
+                out = lpdec.decode_dual(C, d, mu=0.25, max_iter=5000)
+                ms = _time_call(lambda: lpdec.decode_dual(C, d, mu=0.25, max_iter=5000, out=out), 2, 1)
+                it = float(out["iters"].double().sum().item())
+                tiles.append({"group_threads": gt, "groups": g, "ms": ms,
+                              "edge_iters_per_s": it * code.E / (ms / 1000.0)})
+            best = min(tiles, key=lambda r: r["ms"])
+            lpdec.lpdec_dual_set_tile(C.handle, best["group_threads"], best["groups"])
+        for snr in snrs:
+            d = torch.from_numpy(I.awgn_llr(code, snr, F, 9200 + int(10 * snr))).cuda()
+            p = lpdec.make_params(mu=MU, rho=RHO, eps=1e-5, max_iter=1000, state="f32", schedule="resident")
+            out = lpdec.decode(C, d, p)
+            ms = _time_call(lambda: lpdec.decode(C, d, p, out=out), 2, 1)
+            e = A.error_rates(out["bits"].cpu().numpy(), out["iters"].cpu().numpy())
+            rows.append({"code": name, "snr_db": snr, "decoder": "admm", "mu": MU, "rho": RHO, "wer": e["wer"],
+                         "iters_mean": e["iters_mean"], "cert": float(out["cert"].float().mean().item()),
+                         "info_bits_per_s": F * k_info / (ms / 1000.0),
+                         "edge_iters_per_s": e["iters_mean"] * F * code.E / (ms / 1000.0)})
+            for mu in (0.125, 0.25, 0.5):
+                out = lpdec.decode_dual(C, d, mu=mu, max_iter=5000)
+                ms = _time_call(lambda: lpdec.decode_dual(C, d, mu=mu, max_iter=5000, out=out), 2, 1)
+                e = A.error_rates(out["bits"].cpu().numpy(), out["iters"].cpu().numpy())
+                rows.append({"code": name, "snr_db": snr, "decoder": "dual", "mu": mu, "wer": e["wer"],
+                             "iters_mean": e["iters_mean"], "cert": float(out["cert"].float().mean().item()),
+                             "info_bits_per_s": F * k_info / (ms / 1000.0),
+                             "edge_iters_per_s": e["iters_mean"] * F * code.E / (ms / 1000.0)})
+        C.close()
+    print(json.dumps({"workload": "dual", "frames_per_point": F, "dual_max_iter": 5000, "admm_max_iter": 1000,
+                      "admm_eps": 1e-5, "dual_tiles_C1056": tiles, "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -649,6 +701,9 @@ def main():
     if args.workload == "sweep":
         run_sweep(args)
         return
+    if args.workload == "dual":
+        run_dual(args)
+        return
 
     import torch
 
@@ -668,7 +723,11 @@ def main():
     F = len(llr_h)
     C = lpdec.Code(code)
     tile = None
-    if not args.no_autotune:
+    if args.tile:
+        gt, g = (int(v) for v in args.tile.split(","))
+        lpdec.lpdec_set_tile(C.handle, {"f32": 0, "bf16": 1, "f16": 2}[args.state], gt, g)
+        tile = {"group_threads": gt, "groups": g, "source": "--tile"}
+    elif not args.no_autotune:
         sample = torch.from_numpy(np.ascontiguousarray(llr_h[:: max(1, F // 2048)][:2048])).cuda()
         tile = lpdec.lpdec_autotune(C.handle, lpdec.make_params(mu=MU, rho=RHO, eps=0.0, max_iter=60,
                                                                  state=args.state, schedule="resident"),

@@ -315,6 +315,48 @@ LPDEC_API int lpdec_server_destroy(lpdec_server *server);
  */
 LPDEC_API int lpdec_project(int32_t d, int64_t count, const float *v, float *z, void *cuda_stream);
 
+/* ---- dual subgradient decoding (appendix) ------------------------------- */
+
+/*
+ * Decode n_frames frames by dual subgradient ascent on the un-augmented
+ * Lagrangian (the paper's appendix), for comparison with ADMM: from lambda = 0,
+ * each iteration takes, from the same lambda^k,
+ *   x_i = 1 if -gamma_i - sum_{j in N_v(i)} lambda_j^(i) > 0, else 0 (Heaviside),
+ *   z_j = argmax_{z in PP_d} lambda_j^T z (Algorithm 3: the positive entries of
+ *         lambda_j, and when they are odd in number, either the largest
+ *         non-positive entry added, when it costs less than dropping the
+ *         smallest positive entry, or that entry dropped; ties pick the lowest
+ *         index and a tie between the two repairs drops),
+ *   lambda_j += mu (P_j x - z_j),
+ * until the subgradient P_j x - z_j vanishes on every check (then x is an
+ * integral LP optimum, hence an ML codeword) or max_iter iterations ran.
+ * Every decision is taken exactly (lambda is held as integer multiples of mu),
+ * so the outputs equal an exact-arithmetic run of the method.
+ *   code:      from lpdec_code_create, on the current device.
+ *   llr:       device pointer, [n_frames x n] FP32 gamma, frame-major.
+ *   mu:        step size, > 0 and finite.
+ *   max_iter:  1 .. 32767.
+ *   x_out:     device pointer, [n_frames x n] FP32: the final x (0 or 1).
+ *   bits_out:  device pointer, [n_frames x n] uint8, or NULL: the same as bytes.
+ *   iters_out: device pointer, [n_frames] int32, or NULL: iterations run;
+ *              LPDEC_FRAME_BAD_LLR for a frame with a non-finite LLR (its x is 0).
+ *   cert_out:  device pointer, [n_frames] uint8, or NULL: 1 when the
+ *              subgradient vanished (the output is a certified LP optimum).
+ * The call queues work on cuda_stream and returns; it allocates 4 bytes
+ * stream-ordered.  Errors: LPDEC_EINVAL (NULL code, llr or x_out with
+ * n_frames > 0, n_frames < 0, mu or max_iter out of range, a frame state that
+ * does not fit in shared memory), LPDEC_ENOMEM / LPDEC_ECUDA from CUDA.
+ */
+LPDEC_API int lpdec_decode_dual(const lpdec_code *code, int32_t n_frames, const float *llr, double mu,
+                                int32_t max_iter, float *x_out, uint8_t *bits_out, int32_t *iters_out,
+                                uint8_t *cert_out, void *cuda_stream);
+
+/* Tile of lpdec_decode_dual for this code: `groups` frames per CTA, each
+ * decoded by `group_threads` threads (a multiple of 32; groups <= 15; at most
+ * 1024 threads per CTA).  (0, 0) restores the built-in default.  LPDEC_EINVAL
+ * for a tile outside those limits or one whose frame states exceed shared memory. */
+LPDEC_API int lpdec_dual_set_tile(lpdec_code *code, int32_t group_threads, int32_t groups);
+
 #ifdef __cplusplus
 }
 #endif

@@ -50,4 +50,5 @@ struct lpdec_code {
     void *dev_block = nullptr;  // one allocation holding the four index arrays
     int32_t *row_ptr = nullptr, *col_idx = nullptr, *col_ptr = nullptr, *csc_edge = nullptr;
     lpdec::Tile tuned[3];  // per state dtype, from lpdec_autotune
+    lpdec::Tile dual_tile;  // tile of the dual subgradient decoder, from lpdec_dual_set_tile
 };

@@ -41,6 +41,7 @@ EXPORTED = [
     "lpdec_server_create", "lpdec_server_add_code", "lpdec_server_submit", "lpdec_server_poll",
     "lpdec_server_stats", "lpdec_server_destroy", "lpdec_autotune", "lpdec_set_tile", "lpdec_server_counters",
     "lpdec_mixed_plan_create", "lpdec_mixed_plan_decode", "lpdec_mixed_plan_destroy",
+    "lpdec_decode_dual", "lpdec_dual_set_tile",
 ]
 
 
@@ -113,6 +114,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
                                                        ctypes.POINTER(_vp)]),
             "lpdec_mixed_plan_decode": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
             "lpdec_mixed_plan_destroy": (ctypes.c_int, [_vp]),
+            "lpdec_decode_dual": (ctypes.c_int, [_vp, _i32, _vp, ctypes.c_double, _i32, _vp, _vp, _vp, _vp, _vp]),
+            "lpdec_dual_set_tile": (ctypes.c_int, [_vp, _i32, _i32]),
         })
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -270,6 +273,16 @@ def lpdec_project(d, count, v_ptr, z_ptr, stream_ptr) -> None:
     _check(load().lpdec_project(d, count, v_ptr, z_ptr, stream_ptr))
 
 
+def lpdec_decode_dual(handle, n_frames, llr_ptr, mu, max_iter, x_ptr, bits_ptr, iters_ptr, cert_ptr,
+                      stream_ptr) -> None:
+    _check(load().lpdec_decode_dual(handle, n_frames, llr_ptr, float(mu), int(max_iter), x_ptr, bits_ptr,
+                                    iters_ptr, cert_ptr, stream_ptr))
+
+
+def lpdec_dual_set_tile(handle: int, group_threads: int, groups: int) -> None:
+    _check(load().lpdec_dual_set_tile(handle, group_threads, groups))
+
+
 # ---- convenience layer (torch tensors) ---------------------------------------
 
 def make_params(mu=3.0, rho=1.9, eps=1e-5, max_iter=1000, state="f32", cert_tol=1e-2,
@@ -405,6 +418,29 @@ class Server:
         if self.handle:
             lpdec_server_destroy(self.handle)
             self.handle = None
+
+
+def decode_dual(code: Code, llr, mu: float = 0.25, max_iter: int = 5000, stream=None,
+                out: dict | None = None) -> dict:
+    """Dual subgradient decoding (appendix) of a [frames x n] float32 CUDA
+    tensor; returns CUDA tensors x, bits, iters, cert."""
+    import torch
+
+    if not (llr.is_cuda and llr.dtype == torch.float32 and llr.is_contiguous()):
+        raise ValueError("llr must be a contiguous float32 CUDA tensor")
+    F = llr.shape[0]
+    if llr.shape[1] != code.n:
+        raise ValueError("llr must be [frames x n]")
+    if out is None:
+        out = {
+            "x": torch.empty((F, code.n), dtype=torch.float32, device=llr.device),
+            "bits": torch.empty((F, code.n), dtype=torch.uint8, device=llr.device),
+            "iters": torch.empty((F,), dtype=torch.int32, device=llr.device),
+            "cert": torch.empty((F,), dtype=torch.uint8, device=llr.device),
+        }
+    lpdec_decode_dual(code.handle, F, llr.data_ptr(), mu, max_iter, out["x"].data_ptr(), out["bits"].data_ptr(),
+                      out["iters"].data_ptr(), out["cert"].data_ptr(), _stream_ptr(stream))
+    return out
 
 
 def project(v, stream=None):
