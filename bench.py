@@ -156,8 +156,8 @@ def algorithmic_ops_per_frame_iter(code) -> int:
 KERNEL_SOURCES = ("lpdec_device.cuh", "lpdec_kclass.cuh", "lpdec_internal.h")
 MEASURED_TRAFFIC = {
     # "code/schedule": (source hash, bytes per frame per launch, capture)
-    "C1056/resident": ("d32fd46792611e22", (33_850_624 + 1_739_264) / 8000,
-                 "profiles/decode_kernel_resident_C1056_small.md: 8000 frames x 300 iterations in one launch"),
+    "C1056/resident": ("00771f58f322f23b", (33_898_496 + 1_631_744) / 8000,
+                 "profiles/decode_kernel_resident_C1056_small.md: 8000 frames x 300 iterations in one launch (tile 128 x 2)"),
     "C1056/streamed": ("d32fd46792611e22", (236_679_936 + 141_560_320) / 8000,
                  "profiles/decode_kernel_streamed_C1056_small.md: one iteration of 8000 frames per launch"),
 }

@@ -177,6 +177,27 @@ extern "C" int lpdec_code_create(int32_t n, int32_t m, const int32_t *row_ptr, c
         delete c;
         return cuda_error(err, "lpdec_code_create: cudaMemcpy");
     }
+    // Regular codes: 16-bit index block for the regular-form kernels.  Codes
+    // whose indices need more than 16 bits run the generic form instead.
+    if (c->reg_dv > 0 && (E > 65535 || n > 65535 || c->reg_dv > 4)) c->reg_dv = 0;
+    if (c->reg_dv > 0) {
+        c->col16_elems = (int)((E + 7) / 8 * 8);
+        c->idx16_bytes = (int)((size_t)c->col16_elems * 2 + (((size_t)n * 8 + 15) & ~(size_t)15));  // copy16 moves 16-byte units
+        std::vector<uint16_t> h16((size_t)c->idx16_bytes / 2, 0);
+        for (int64_t e = 0; e < E; ++e) h16[(size_t)e] = (uint16_t)col_idx[e];
+        uint16_t *csc = h16.data() + c->col16_elems;
+        for (int i = 0; i < n; ++i)
+            for (int s = col_ptr[i]; s < col_ptr[i + 1]; ++s) csc[(size_t)i * 4 + (s - col_ptr[i])] = (uint16_t)edge_perm[s];
+        err = cudaMalloc(&c->dev_idx16, (size_t)c->idx16_bytes);
+        if (err == cudaSuccess)
+            err = cudaMemcpy(c->dev_idx16, h16.data(), (size_t)c->idx16_bytes, cudaMemcpyHostToDevice);
+        if (err != cudaSuccess) {
+            cudaFree(c->dev_idx16);
+            cudaFree(c->dev_block);
+            delete c;
+            return cuda_error(err, "lpdec_code_create: 16-bit index block");
+        }
+    }
     *out = c;
     return LPDEC_OK;
 }
@@ -195,6 +216,10 @@ extern "C" int lpdec_code_info(const lpdec_code *c, int32_t *n, int32_t *m, int6
 extern "C" int lpdec_code_destroy(lpdec_code *c) {
     if (!c) return set_error(LPDEC_EINVAL, "lpdec_code_destroy: code is NULL");
     cudaError_t err = cudaFree(c->dev_block);
+    if (c->dev_idx16) {
+        cudaError_t e2 = cudaFree(c->dev_idx16);
+        if (err == cudaSuccess) err = e2;
+    }
     delete c;
     if (err != cudaSuccess) return cuda_error(err, "lpdec_code_destroy: cudaFree");
     return LPDEC_OK;
@@ -204,22 +229,22 @@ extern "C" int lpdec_code_destroy(lpdec_code *c) {
 // launch plumbing
 namespace lpdec {
 
-static cudaError_t class_prepare(const lpdec_code *c, int dtype, size_t smem) {
+static cudaError_t class_prepare(const lpdec_code *c, int dtype, bool stage, size_t smem) {
     switch (kClassD[c->cls]) {
-        case 6: return prepare_decode_6(dtype, c->reg_dv, smem);
-        case 8: return prepare_decode_8(dtype, c->reg_dv, smem);
-        case 16: return prepare_decode_16(dtype, c->reg_dv, smem);
-        case 20: return prepare_decode_20(dtype, c->reg_dv, smem);
-        default: return prepare_decode_32(dtype, c->reg_dv, smem);
+        case 6: return prepare_decode_6(dtype, c->reg_dv, stage, smem);
+        case 8: return prepare_decode_8(dtype, c->reg_dv, stage, smem);
+        case 16: return prepare_decode_16(dtype, c->reg_dv, stage, smem);
+        case 20: return prepare_decode_20(dtype, c->reg_dv, stage, smem);
+        default: return prepare_decode_32(dtype, c->reg_dv, stage, smem);
     }
 }
-static cudaError_t class_occupancy(const lpdec_code *c, int dtype, int block, size_t smem, int *bps) {
+static cudaError_t class_occupancy(const lpdec_code *c, int dtype, bool stage, int block, size_t smem, int *bps) {
     switch (kClassD[c->cls]) {
-        case 6: return occupancy_decode_6(dtype, c->reg_dv, block, smem, bps);
-        case 8: return occupancy_decode_8(dtype, c->reg_dv, block, smem, bps);
-        case 16: return occupancy_decode_16(dtype, c->reg_dv, block, smem, bps);
-        case 20: return occupancy_decode_20(dtype, c->reg_dv, block, smem, bps);
-        default: return occupancy_decode_32(dtype, c->reg_dv, block, smem, bps);
+        case 6: return occupancy_decode_6(dtype, c->reg_dv, stage, block, smem, bps);
+        case 8: return occupancy_decode_8(dtype, c->reg_dv, stage, block, smem, bps);
+        case 16: return occupancy_decode_16(dtype, c->reg_dv, stage, block, smem, bps);
+        case 20: return occupancy_decode_20(dtype, c->reg_dv, stage, block, smem, bps);
+        default: return occupancy_decode_32(dtype, c->reg_dv, stage, block, smem, bps);
     }
 }
 static cudaError_t class_launch(const lpdec_code *c, int dtype, const DecodeArgs &a, const LaunchCfg &lc) {
@@ -300,17 +325,26 @@ Tile default_tile(const lpdec_code *c, int dtype, int max_threads) {
 int plan_launch(const lpdec_code *c, int dtype, const Tile &tile, int n_frames, cudaStream_t stream,
                 LaunchCfg *lc, SliceLayout *layout) {
     const SliceLayout L = slice_layout(c, dtype, tile.group_threads);
-    const size_t smem = L.bytes * (size_t)tile.groups;
+    size_t smem = L.bytes * (size_t)tile.groups;
     if ((int)smem > device_smem_optin(c->device) || tile.groups < 1)
         return set_error(LPDEC_EINVAL, "frame state (%zu bytes per group x %d groups) does not fit in shared memory (%d bytes)",
                          L.bytes, tile.groups, device_smem_optin(c->device));
     const int block = tile.groups * tile.group_threads;
     if (block > class_max_threads(c->cls) || tile.groups > 15 || tile.group_threads % 32)
         return set_error(LPDEC_EINVAL, "invalid tile: %d groups x %d threads", tile.groups, tile.group_threads);
-    cudaError_t err = class_prepare(c, dtype, smem);
+    // Regular form: stage the 16-bit index block at the start of shared memory
+    // (the slices follow it) when it fits.
+    lc->slice_base = 0;
+    const size_t idx_aligned = ((size_t)c->idx16_bytes + 127) & ~(size_t)127;
+    if (c->reg_dv > 0 && c->idx16_bytes > 0 && smem + idx_aligned <= (size_t)device_smem_optin(c->device)) {
+        lc->slice_base = (int)idx_aligned;
+        smem += idx_aligned;
+    }
+    const bool stage = lc->slice_base > 0;
+    cudaError_t err = class_prepare(c, dtype, stage, smem);
     if (err != cudaSuccess) return cuda_error(err, "cudaFuncSetAttribute");
     int bps = 0;
-    err = class_occupancy(c, dtype, block, smem, &bps);
+    err = class_occupancy(c, dtype, stage, block, smem, &bps);
     if (err != cudaSuccess) return cuda_error(err, "occupancy query");
     if (bps < 1) return set_error(LPDEC_EINVAL, "tile does not fit on an SM (%d threads, %zu bytes)", block, smem);
     const long long need = ((long long)n_frames + tile.groups - 1) / tile.groups;
@@ -343,6 +377,7 @@ IterCfg make_cfg(const lpdec_code *c, const lpdec_params *p) {
     cfg.mu_inv = (float)(1.0 / p->mu);
     cfg.rho = (float)p->rho;
     cfg.omr = (float)(1.0 - p->rho);
+    cfg.tmr = (float)(2.0 - p->rho);
     cfg.cert_tol = (float)p->cert_tol;
     cfg.eps2E = p->eps * p->eps * (double)c->E;
     const double epsc = std::max(p->eps, 1e-5);
@@ -362,6 +397,10 @@ CodeView make_view(const lpdec_code *c) {
     v.col_idx = c->col_idx;
     v.col_ptr = c->col_ptr;
     v.csc_edge = c->csc_edge;
+    v.col16 = static_cast<const uint16_t *>(c->dev_idx16);
+    v.csc16 = c->dev_idx16 ? v.col16 + c->col16_elems : nullptr;
+    v.idx16_bytes = c->idx16_bytes;
+    v.col16_elems = c->col16_elems;
     return v;
 }
 
@@ -406,6 +445,7 @@ int enqueue_decode(const lpdec_code *c, int n_frames, const float *llr, const lp
     a.smem_per_group = (int)L.bytes;
     a.off_x = (int)L.off_x;
     a.off_red = (int)L.off_red;
+    a.slice_base = lc.slice_base;
     const int ipl = schedule == LPDEC_SCHED_STREAMED ? p->iters_per_launch : p->max_iter;
     const int launches = schedule == LPDEC_SCHED_STREAMED ? (p->max_iter + ipl - 1) / ipl : 1;
     char *w = static_cast<char *>(work);
@@ -413,7 +453,7 @@ int enqueue_decode(const lpdec_code *c, int n_frames, const float *llr, const lp
     size_t off = (256 + (size_t)launches * 4 + 255) & ~(size_t)255;
     if (schedule == LPDEC_SCHED_STREAMED) {
         const size_t sb = (size_t)n_frames * c->Ep * dtype_size(p->state_dtype);
-        a.z_state = w + off;
+        a.w_state = w + off;
         a.l_state = w + off + sb;
         a.k_state = reinterpret_cast<int32_t *>(w + off + 2 * sb);
         cudaError_t err = cudaMemsetAsync(a.k_state, 0, (size_t)n_frames * 4, stream);
@@ -442,6 +482,7 @@ int launch_once(const lpdec_code *c, int dtype, const Tile &tile, DecodeArgs &a,
     a.smem_per_group = (int)L.bytes;
     a.off_x = (int)L.off_x;
     a.off_red = (int)L.off_red;
+    a.slice_base = lc.slice_base;
     cudaError_t err = class_launch(c, dtype, a, lc);
     if (err != cudaSuccess) return cuda_error(err, "decode kernel launch");
     return LPDEC_OK;

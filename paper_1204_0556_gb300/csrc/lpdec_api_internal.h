@@ -49,6 +49,9 @@ struct lpdec_code {
     int reg_dv = 0;             // variable degree if the code is regular with check degree == class D, else 0
     void *dev_block = nullptr;  // one allocation holding the four index arrays
     int32_t *row_ptr = nullptr, *col_idx = nullptr, *col_ptr = nullptr, *csc_edge = nullptr;
+    // Regular codes: 16-bit index block (CodeView::col16 / csc16), else null.
+    void *dev_idx16 = nullptr;
+    int idx16_bytes = 0, col16_elems = 0;
     lpdec::Tile tuned[3];  // per state dtype, from lpdec_autotune
     lpdec::Tile dual_tile;  // tile of the dual subgradient decoder, from lpdec_dual_set_tile
 };

@@ -5,17 +5,18 @@
 // decodes one frame at a time; a CTA holds G groups, each with its own slice
 // of shared memory and its own named barrier.  Inside a group:
 //   - variable phase: thread t owns variables t, t+GT, ...; it sums
-//     z_e - lambda_e/mu over the variable's edges (CSC order, gathered through
-//     the edge permutation) and writes x_i (Algorithm 1, x-update);
+//     w_e = z_e - lambda_e/mu over the variable's edges (CSC order, gathered
+//     through the edge permutation) and writes x_i (Algorithm 1, x-update);
 //   - check phase: thread t owns checks t, t+GT, ...; it gathers x over the
-//     check's edges, forms the over-relaxed v, projects it onto PP_d in
-//     registers and writes z and lambda back (Algorithm 1, z- and
-//     lambda-updates);
+//     check's edges, recovers z_old = w + lambda/mu, forms the over-relaxed v,
+//     projects it onto PP_d in registers and writes lambda/mu = v - z and
+//     w = z - lambda/mu back (Algorithm 1, z- and lambda-updates);
 //   - stopping test: FP32 per-thread partials, FP32 warp shuffles, FP64 sum
 //     over the group's warps (the only FP64 on the GPU).
-// The z and lambda state is stored as S (float, bf16 or fp16); all
+// The edge state (w, lambda/mu) is stored as S (float, bf16 or fp16); all
 // arithmetic is FP32.  lambda is kept pre-scaled as lambda/mu (the scaled
-// dual of Section 3.4), so the lambda-update is lambda' <- v - z.
+// dual of Section 3.4), so the lambda-update is lambda' <- v - z.  Keeping w
+// rather than z halves the x-update's gathers; it is the same iteration.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -107,13 +108,13 @@ template <int D>
 __device__ __forceinline__ float beta_sorted(float (&kap)[D], int d) {
     sort_asc<D>(kap);
     float P = 1.0f + kap[0];
-    float bn = P, bd = 1.0f;
+    float best = P;
 #pragma unroll
     for (int m = 2; m <= D; ++m) {
         P += kap[m - 1];
-        if (m <= d && P * bd < bn * (float)m) { bn = P; bd = (float)m; }
+        if (m <= d) best = fminf(best, P * (1.0f / (float)m));  // 1/m folds to a constant
     }
-    return fmaxf(__fdividef(bn, bd), 0.0f);
+    return fmaxf(best, 0.0f);
 }
 
 // Michelot-style fixed point for large D (no sort, no kappa array): start
@@ -168,31 +169,42 @@ __device__ __forceinline__ float proj_z(float v, const Proj &pr, int k) {
     return __saturatef(((pr.facet >> k) & 1u) ? v - pr.beta : v + pr.beta);
 }
 
+//
+// Facet and violation test in one pass.  With zh = clip(v) and
+// delta_k = |zh_k - 1/2|, zh_k = 1/2 + delta_k on S and 1/2 - delta_k off S, so
+// for the odd set S the facet value is g = |S| - d/2 + sum_k delta_k, and
+// g > |S| - 1 reads  sum_k delta_k > d/2 - 1.  Flipping entry kb (when the
+// set {zh > 1/2} is even) lowers the left side by 2 delta_kb either way.  The
+// entry closest to 1/2 is found with one integer min over keys holding
+// delta's bit pattern (nonnegative floats order as integers) with its low
+// bits replaced by the index; entries whose distances agree to within those
+// bits are tied and the lowest index wins.
 template <int D>
 __device__ __forceinline__ Proj project_pp(const float (&v)[D], int d) {
     static_assert(D >= 1 && D <= 32, "check degree above 32");
+    constexpr int kIdxBits = D <= 8 ? 3 : 5;
+    constexpr int kIdxMask = (1 << kIdxBits) - 1;
     unsigned th = 0u;
-    int kb = 0;
-    float best = 2.0f;
+    int key = 0x7fffffff;
+    float sdist = 0.0f;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
         const float zh = __saturatef(v[k]);
         if (zh > 0.5f) th |= 1u << k;
         const float dist = fabsf(zh - 0.5f);
-        if (k < d && dist < best) { best = dist; kb = k; }
+        if (k < d) {
+            sdist += dist;
+            key = min(key, (__float_as_int(dist) & ~kIdxMask) | k);
+        }
     }
-    if ((__popc(th) & 1) == 0) th ^= 1u << kb;
-    const int s = __popc(th);
-    float g = 0.0f;
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-        const float zh = __saturatef(v[k]);
-        g += ((th >> k) & 1u) ? zh : -zh;
+    if ((__popc(th) & 1) == 0) {
+        th ^= 1u << (key & kIdxMask);
+        sdist -= 2.0f * __int_as_float(key & ~kIdxMask);
     }
     Proj pr;
     pr.facet = th;
     pr.beta = 0.0f;
-    if (g <= (float)(s - 1)) return pr;  // zh already in PP_d
+    if (sdist <= 0.5f * (float)d - 1.0f) return pr;  // zh already in PP_d
 
     if constexpr (D <= 8) {
         float kap[D];
@@ -214,12 +226,22 @@ struct CodeView {
     const int *col_idx;       // [E]   variable of each CSR edge
     const int *col_ptr;       // [n+1] CSC
     const int *csc_edge;      // [E]   CSR edge id of each CSC slot
+    // Regular codes only (null otherwise): 16-bit copies of the indices, in one
+    // block of idx16_bytes (a multiple of 16): col16[col16_elems] = col_idx
+    // (CSR order, padded to a multiple of 8 entries), then csc16[4n] = the CSR
+    // edge ids of each variable's edges in 4 slots (unused slots 0).  Global
+    // memory, or the CTA's shared-memory copy (generic pointers).
+    const uint16_t *col16;
+    const uint16_t *csc16;
+    int idx16_bytes;
+    int col16_elems;
 };
 
 struct IterCfg {
     float mu_inv;       // 1/mu
     float rho;          // over-relaxation
     float omr;          // 1 - rho
+    float tmr;          // 2 - rho
     float cert_tol;
     double eps2E;       // eps^2 * E
     double epsc2E;      // max(eps, 1e-5)^2 * E
@@ -237,7 +259,7 @@ struct DecodeArgs {
     int32_t *iters_out;      // [F] or null
     uint8_t *cert_out;       // [F] or null
     // STREAMED schedule: state kept in device memory between launches (null when RESIDENT)
-    void *z_state;           // [F x Ep] of S
+    void *w_state;           // [F x Ep] of S (w = z - lambda/mu)
     void *l_state;           // [F x Ep] of S (lambda/mu)
     int32_t *k_state;        // [F] iterations done; -1 once the frame is finished
     int iters_this_launch;   // RESIDENT: max_iter
@@ -247,6 +269,8 @@ struct DecodeArgs {
     int smem_per_group;      // bytes of one group's slice
     int off_x;               // byte offset of x in a slice
     int off_red;             // byte offset of the reduction scratch in a slice
+    int slice_base;          // byte offset of the first slice: 0, or (staged regular form) the
+                             // 128-aligned size of the 16-bit index block copied to offset 0
 };
 
 // Named barrier for one group (ids 1..15; id 0 is __syncthreads).
@@ -267,17 +291,20 @@ __device__ __forceinline__ float warp_max(float v) {
 
 
 // One check update (Algorithm 1 z- and lambda-update with over-relaxation),
-// by one thread, in registers.  For small D the gathered x and old z stay in
+// by one thread, in registers.  The edge state is (w, l) = (z - lambda/mu,
+// lambda/mu); z_old = w + l.  For small D the gathered x and old z stay in
 // registers; for large D they are re-read from shared memory in the store
 // pass to keep the register footprint at one D-array.
 // DV > 0: the code is regular (every check has degree D, so check j owns
 // edges j*D .. j*D+D-1, and every variable has degree DV); the edge state of a
 // check is then read and written in aligned pairs.
-template <int D, int DV, typename S>
+// RES: also accumulate the primal and dual residual terms (iterations that run
+// the stopping test or produce the certificate); without them z_old is not
+// needed and v = rho x + (1 - rho) w + (2 - rho) lambda/mu directly.
+template <int D, int DV, typename S, bool RES>
 __device__ __forceinline__ void check_update(const CodeView &c, const IterCfg &p, int j,
-                                             S *zs, S *ls, const float *xs, bool need_res,
-                                             float &rp, float &rd) {
-    constexpr bool kKeep = D <= 8;
+                                             S *ws, S *ls, const float *xs, float &rp, float &rd) {
+    constexpr bool kKeep = RES && D <= 8;
     constexpr bool kReg = DV > 0;
     constexpr bool kPairs = kReg && (D % 2 == 0);
     const int e0 = kReg ? j * D : __ldg(c.row_ptr + j);
@@ -285,16 +312,22 @@ __device__ __forceinline__ void check_update(const CodeView &c, const IterCfg &p
     float v[D];
     float xv[kKeep ? D : 1], zo[kKeep ? D : 1];
     if constexpr (kPairs) {
-        const int2 *ci = reinterpret_cast<const int2 *>(c.col_idx + e0);
+        const uint32_t *ci = reinterpret_cast<const uint32_t *>(c.col16 + e0);
 #pragma unroll
         for (int k = 0; k < D; k += 2) {
-            const int2 cc = __ldg(ci + k / 2);
-            const float x0 = xs[cc.x], x1 = xs[cc.y];
-            const float2 z2 = ld2<S>(zs + e0 + k);
+            const uint32_t cc = ci[k / 2];
+            const float x0 = xs[cc & 0xffffu], x1 = xs[cc >> 16];
+            const float2 w2 = ld2<S>(ws + e0 + k);
             const float2 l2 = ld2<S>(ls + e0 + k);
-            if constexpr (kKeep) { xv[k] = x0; xv[k + 1] = x1; zo[k] = z2.x; zo[k + 1] = z2.y; }
-            v[k] = fmaf(p.rho, x0, p.omr * z2.x) + l2.x;
-            v[k + 1] = fmaf(p.rho, x1, p.omr * z2.y) + l2.y;
+            if constexpr (RES) {
+                const float z0 = w2.x + l2.x, z1 = w2.y + l2.y;  // z_old
+                if constexpr (kKeep) { xv[k] = x0; xv[k + 1] = x1; zo[k] = z0; zo[k + 1] = z1; }
+                v[k] = fmaf(p.rho, x0, p.omr * z0) + l2.x;
+                v[k + 1] = fmaf(p.rho, x1, p.omr * z1) + l2.y;
+            } else {
+                v[k] = fmaf(p.rho, x0, fmaf(p.omr, w2.x, p.tmr * l2.x));
+                v[k + 1] = fmaf(p.rho, x1, fmaf(p.omr, w2.y, p.tmr * l2.y));
+            }
         }
     } else {
 #pragma unroll
@@ -302,10 +335,15 @@ __device__ __forceinline__ void check_update(const CodeView &c, const IterCfg &p
             if (k < d) {
                 const int e = e0 + k;
                 const float xk = xs[__ldg(c.col_idx + e)];
-                const float zk = ld<S>(zs[e]);
-                if constexpr (kKeep) { xv[k] = xk; zo[k] = zk; }
-                const float q = fmaf(p.rho, xk, p.omr * zk);  // rho P_j x + (1 - rho) z_j^old
-                v[k] = q + ld<S>(ls[e]);                       // v_j = q + lambda_j / mu
+                const float lk = ld<S>(ls[e]);
+                if constexpr (RES) {
+                    const float zk = ld<S>(ws[e]) + lk;  // z_j^old
+                    if constexpr (kKeep) { xv[k] = xk; zo[k] = zk; }
+                    const float q = fmaf(p.rho, xk, p.omr * zk);  // rho P_j x + (1 - rho) z_j^old
+                    v[k] = q + lk;                                 // v_j = q + lambda_j / mu
+                } else {
+                    v[k] = fmaf(p.rho, xk, fmaf(p.omr, ld<S>(ws[e]), p.tmr * lk));
+                }
             } else {
                 v[k] = kPadV;
             }
@@ -316,9 +354,10 @@ __device__ __forceinline__ void check_update(const CodeView &c, const IterCfg &p
 #pragma unroll
         for (int k = 0; k < D; k += 2) {
             const float z0 = proj_z(v[k], pr, k), z1 = proj_z(v[k + 1], pr, k + 1);
-            st2<S>(zs + e0 + k, z0, z1);
-            st2<S>(ls + e0 + k, v[k] - z0, v[k + 1] - z1);  // lambda/mu = v - z
-            if (need_res) {
+            const float l0 = v[k] - z0, l1 = v[k + 1] - z1;  // lambda/mu = v - z
+            st2<S>(ls + e0 + k, l0, l1);
+            st2<S>(ws + e0 + k, z0 - l0, z1 - l1);
+            if constexpr (RES) {
                 float a = xv[k] - z0, b = z0 - zo[k];
                 rp = fmaf(a, a, rp);
                 rd = fmaf(b, b, rd);
@@ -336,10 +375,11 @@ __device__ __forceinline__ void check_update(const CodeView &c, const IterCfg &p
                 const float z = proj_z(v[k], pr, k);
                 float xk = 0.0f, zk = 0.0f;
                 if constexpr (kKeep) { xk = xv[k]; zk = zo[k]; }
-                else if (need_res) { xk = xs[__ldg(c.col_idx + e)]; zk = ld<S>(zs[e]); }
-                zs[e] = st<S>(z);
-                ls[e] = st<S>(v[k] - z);  // lambda/mu += q - z, i.e. lambda/mu = v - z
-                if (need_res) {
+                else if constexpr (RES) { xk = xs[__ldg(c.col_idx + e)]; zk = ld<S>(ws[e]) + ld<S>(ls[e]); }
+                const float l = v[k] - z;  // lambda/mu += q - z, i.e. lambda/mu = v - z
+                ls[e] = st<S>(l);
+                ws[e] = st<S>(z - l);
+                if constexpr (RES) {
                     const float a = xk - z;
                     const float b = z - zk;
                     rp = fmaf(a, a, rp);
@@ -371,7 +411,7 @@ __device__ __forceinline__ int seg_sum_i(int x) {
 
 template <int D, int L, typename S>
 __device__ __forceinline__ void check_update_seg(const CodeView &c, const IterCfg &p, int j, bool valid,
-                                                 S *zs, S *ls, const float *xs, bool need_res,
+                                                 S *ws, S *ls, const float *xs, bool need_res,
                                                  float &rp, float &rd) {
     constexpr int V = (D + L - 1) / L;
     const int r = threadIdx.x & (L - 1);
@@ -387,8 +427,9 @@ __device__ __forceinline__ void check_update_seg(const CodeView &c, const IterCf
         if (q < d) {
             const int e = e0 + q;
             const float xk = xs[__ldg(c.col_idx + e)];
-            const float zk = ld<S>(zs[e]);
-            v[k] = fmaf(p.rho, xk, p.omr * zk) + ld<S>(ls[e]);
+            const float lk = ld<S>(ls[e]);
+            const float zk = ld<S>(ws[e]) + lk;  // z_old
+            v[k] = fmaf(p.rho, xk, p.omr * zk) + lk;
         } else {
             v[k] = kPadV;
         }
@@ -472,21 +513,25 @@ __device__ __forceinline__ void check_update_seg(const CodeView &c, const IterCf
             const float z = proj_z(v[k], pr, k);
             if (need_res) {
                 const float a = xs[__ldg(c.col_idx + e)] - z;
-                const float b = z - ld<S>(zs[e]);
+                const float b = z - (ld<S>(ws[e]) + ld<S>(ls[e]));
                 rp = fmaf(a, a, rp);
                 rd = fmaf(b, b, rd);
             }
-            zs[e] = st<S>(z);
-            ls[e] = st<S>(v[k] - z);
+            const float l = v[k] - z;
+            ls[e] = st<S>(l);
+            ws[e] = st<S>(z - l);
         }
     }
 }
 
-// Shared-memory slice of one group: z[Ep], l[Ep] (type S), x[n] (float),
+// Shared-memory slice of one group: w[Ep], l[Ep] (type S), x[n] (float),
 // red[2 * nwarps] (float), flags[8] (int; the last two hold an mbarrier).
+// The edge state is kept as w = z - lambda/mu and l = lambda/mu: the x-update
+// needs only the sum of w over a variable's edges (one gather per edge), and
+// the check update recovers z_old = w + l.
 template <typename S>
 struct Slice {
-    S *z, *l;
+    S *w, *l;
     float *x, *red;
     int *flags;      // [0] converged, [1] residual ok, [2] bad LLR, [3] copy ok, [4..5] frame ids
     uint64_t *mbar;  // flags[6..7]: completion barrier of the bulk loads
@@ -571,7 +616,7 @@ struct FrameIO {
     uint8_t *bits;      // [n] or null
     int32_t *iters;     // one value or null
     uint8_t *cert;      // one value or null
-    void *z_state;      // STREAMED: [Ep] of S
+    void *w_state;      // STREAMED: [Ep] of S
     void *l_state;      // STREAMED: [Ep] of S
     int32_t *k_state;   // STREAMED: iterations done (-1: finished); null when RESIDENT
 };
@@ -592,10 +637,10 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
     if (t == 0) { flags[0] = 0; flags[1] = 0; flags[2] = 0; }
 
     if (k == 0) {
-        // Algorithm 1 initialization: z = lambda = 0.  Also reject non-finite LLRs.
+        // Algorithm 1 initialization: z = lambda = 0 (w = 0).  Also reject non-finite LLRs.
         int bad = 0;
         for (int i = t; i < c.n; i += T) bad |= !isfinite(__ldg(gam + i));
-        zero16(sm.z, 2 * state_bytes, t, T);
+        zero16(sm.w, 2 * state_bytes, t, T);
         bad = __any_sync(0xffffffffu, bad);
         group_sync(bar, T);
         if (bad && lane == 0) atomicOr((int *)&flags[2], 1);
@@ -613,13 +658,13 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
             return true;
         }
     } else {
-        // STREAMED: bring the parked z and lambda/mu back with two bulk copies.
-        const void *zg = io.z_state;
+        // STREAMED: bring the parked w and lambda/mu back with two bulk copies.
+        const void *zg = io.w_state;
         const void *lg = io.l_state;
         if (t == 0) {
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(sm.mbar, 2u * (uint32_t)state_bytes);
-            bulk_load(sm.z, zg, (uint32_t)state_bytes, sm.mbar);
+            bulk_load(sm.w, zg, (uint32_t)state_bytes, sm.mbar);
             bulk_load(sm.l, lg, (uint32_t)state_bytes, sm.mbar);
             flags[3] = mbar_wait_bounded(sm.mbar, phase) ? 1 : 0;
         }
@@ -640,21 +685,21 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
     const int k_end = min(p.max_iter, k + iters_this_launch);
     bool conv = false, rok = false;
     while (k < k_end) {
-        // ---- x-update (Algorithm 1; Section 3.2)
+        // ---- x-update (Algorithm 1; Section 3.2): sum over the edges of w = z - lambda/mu
         for (int i = t; i < c.n; i += T) {
             float acc = 0.0f, inv_dv;
             if constexpr (DV > 0) {
+                static_assert(DV <= 4, "regular form holds up to 4 edges per variable");
+                const uint2 pk = *reinterpret_cast<const uint2 *>(c.csc16 + 4 * i);
+                const unsigned es[4] = {pk.x & 0xffffu, pk.x >> 16, pk.y & 0xffffu, pk.y >> 16};
 #pragma unroll
-                for (int s = 0; s < DV; ++s) {
-                    const int e = __ldg(c.csc_edge + i * DV + s);
-                    acc += ld<S>(sm.z[e]) - ld<S>(sm.l[e]);
-                }
+                for (int s = 0; s < DV; ++s) acc += ld<S>(sm.w[es[s]]);
                 inv_dv = 1.0f / (float)DV;
             } else {
                 const int s0 = __ldg(c.col_ptr + i), s1 = __ldg(c.col_ptr + i + 1);
                 for (int s = s0; s < s1; ++s) {
                     const int e = __ldg(c.csc_edge + s);
-                    acc += ld<S>(sm.z[e]) - ld<S>(sm.l[e]);
+                    acc += ld<S>(sm.w[e]);
                 }
                 inv_dv = __frcp_rn((float)(s1 - s0));
             }
@@ -666,12 +711,16 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
         const bool need_res = p.check_stop || (k + 1 == p.max_iter);
         float rp = 0.0f, rd = 0.0f;
         if constexpr (L == 1) {
-            for (int j = t; j < c.m; j += T) check_update<D, DV, S>(c, p, j, sm.z, sm.l, sm.x, need_res, rp, rd);
+            if (need_res) {
+                for (int j = t; j < c.m; j += T) check_update<D, DV, S, true>(c, p, j, sm.w, sm.l, sm.x, rp, rd);
+            } else {
+                for (int j = t; j < c.m; j += T) check_update<D, DV, S, false>(c, p, j, sm.w, sm.l, sm.x, rp, rd);
+            }
         } else {
             const int per_pass = T / L;
             for (int j0 = 0; j0 < c.m; j0 += per_pass) {
                 const int j = j0 + t / L;
-                check_update_seg<D, L, S>(c, p, j, j < c.m, sm.z, sm.l, sm.x, need_res, rp, rd);
+                check_update_seg<D, L, S>(c, p, j, j < c.m, sm.w, sm.l, sm.x, need_res, rp, rd);
             }
         }
         ++k;
@@ -703,7 +752,7 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
         // slice waits for the stores to finish reading it.
         if (t == 0) {
             fence_proxy_async_smem();
-            bulk_store(io.z_state, sm.z, (uint32_t)state_bytes);
+            bulk_store(io.w_state, sm.w, (uint32_t)state_bytes);
             bulk_store(io.l_state, sm.l, (uint32_t)state_bytes);
             bulk_commit();
             *io.k_state = k;
@@ -746,18 +795,28 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
 // Persistent decode kernel: each group pulls frame ids from a global counter
 // until the batch is exhausted.  DV > 0 selects the regular-code form (check
 // degree D, variable degree DV); L is the number of lanes per check.  MAXT:
-// largest CTA size the kernel is built for.
-template <int D, int L, int DV, typename S, int MAXT>
+// largest CTA size the kernel is built for.  STAGE (regular form only): the
+// CTA first copies the code's 16-bit index block to the start of its shared
+// memory and reads the indices from there; the slices follow at slice_base.
+template <int D, int L, int DV, typename S, int MAXT, bool STAGE>
 __global__ void __launch_bounds__(MAXT, 1) decode_kernel(const DecodeArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    static_assert(!STAGE || DV > 0, "index staging is built for the regular form");
+    CodeView cv = a.code;
+    if constexpr (STAGE) {
+        copy16(smem_raw, a.code.col16, a.code.idx16_bytes, threadIdx.x, blockDim.x);
+        __syncthreads();
+        cv.col16 = reinterpret_cast<const uint16_t *>(smem_raw);
+        cv.csc16 = cv.col16 + a.code.col16_elems;
+    }
     const int T = a.group_threads;
     const int g = threadIdx.x / T;
     const int t = threadIdx.x - g * T;
     const int bar = 1 + g;
-    unsigned char *base = smem_raw + (size_t)g * a.smem_per_group;
+    unsigned char *base = smem_raw + a.slice_base + (size_t)g * a.smem_per_group;
     Slice<S> sm;
-    sm.z = reinterpret_cast<S *>(base);
-    sm.l = sm.z + a.code.Ep;
+    sm.w = reinterpret_cast<S *>(base);
+    sm.l = sm.w + a.code.Ep;
     sm.x = reinterpret_cast<float *>(base + a.off_x);
     sm.red = reinterpret_cast<float *>(base + a.off_red);
     sm.flags = reinterpret_cast<int *>(sm.red + 2 * (T >> 5));
@@ -791,14 +850,14 @@ __global__ void __launch_bounds__(MAXT, 1) decode_kernel(const DecodeArgs a) {
         io.cert = a.cert_out ? a.cert_out + f : nullptr;
         if (a.k_state) {
             const size_t sb = (size_t)a.code.Ep * sizeof(S);
-            io.z_state = reinterpret_cast<char *>(a.z_state) + (size_t)f * sb;
+            io.w_state = reinterpret_cast<char *>(a.w_state) + (size_t)f * sb;
             io.l_state = reinterpret_cast<char *>(a.l_state) + (size_t)f * sb;
             io.k_state = a.k_state + f;
         } else {
-            io.z_state = io.l_state = nullptr;
+            io.w_state = io.l_state = nullptr;
             io.k_state = nullptr;
         }
-        if (!frame_run<D, L, DV, S>(a.code, a.cfg, a.iters_this_launch, io, sm, t, T, bar, phase)) break;
+        if (!frame_run<D, L, DV, S>(cv, a.cfg, a.iters_this_launch, io, sm, t, T, bar, phase)) break;
     }
     if (t == 0) bulk_wait_all();
 }

@@ -44,6 +44,8 @@ struct LaunchCfg {
     int block;
     size_t smem;
     cudaStream_t stream;
+    int slice_base = 0;  // staged regular form: shared-memory offset of the first slice (after the
+                         // 16-bit index block at offset 0); 0 when the indices are not staged
 };
 
 // Per-class entry points, defined in lpdec_kD.cu.
@@ -51,8 +53,9 @@ struct LaunchCfg {
 // exactly D (selects the regular-code kernel where one is built), else 0.
 #define LPDEC_DECLARE_CLASS(D)                                                                           \
     cudaError_t launch_decode_##D(int dtype, int reg_dv, const DecodeArgs &a, const LaunchCfg &lc);      \
-    cudaError_t occupancy_decode_##D(int dtype, int reg_dv, int block, size_t smem, int *blocks_per_sm); \
-    cudaError_t prepare_decode_##D(int dtype, int reg_dv, size_t smem);                                  \
+    cudaError_t occupancy_decode_##D(int dtype, int reg_dv, bool stage, int block, size_t smem,            \
+                                     int *blocks_per_sm);                                                 \
+    cudaError_t prepare_decode_##D(int dtype, int reg_dv, bool stage, size_t smem);                      \
     cudaError_t launch_project_##D(int d, long long count, const float *v, float *z, cudaStream_t s);
 LPDEC_DECLARE_CLASS(6)
 LPDEC_DECLARE_CLASS(8)

@@ -21,32 +21,44 @@ constexpr int kMaxT = class_max_threads_D(kD);
 // Variable degree of the regular-code kernel built for this class (0: none).
 constexpr int kRegDV = kD == 6 ? 3 : (kD == 8 ? 4 : 0);
 
-template <int DV, typename S>
+// Kernel forms of this class: 0 generic, 1 regular (indices from global
+// memory), 2 regular with the indices staged in shared memory.
+constexpr int kForms = 3;
+
+template <int DV, bool STAGE, typename S>
 const void *decode_fn() {
-    return reinterpret_cast<const void *>(&decode_kernel<kD, kL, DV, S, kMaxT>);
+    return reinterpret_cast<const void *>(&decode_kernel<kD, kL, DV, S, kMaxT, STAGE>);
 }
 
-template <int DV>
+template <int DV, bool STAGE>
 const void *decode_fn_dtype(int dtype) {
     switch (dtype) {
-        case 0: return decode_fn<DV, float>();
-        case 1: return decode_fn<DV, __nv_bfloat16>();
-        case 2: return decode_fn<DV, __half>();
+        case 0: return decode_fn<DV, STAGE, float>();
+        case 1: return decode_fn<DV, STAGE, __nv_bfloat16>();
+        case 2: return decode_fn<DV, STAGE, __half>();
         default: return nullptr;
     }
 }
 
-const void *decode_fn_for(int dtype, int reg_dv) {
-    if (kRegDV > 0 && reg_dv == kRegDV) return decode_fn_dtype<kRegDV>(dtype);
-    return decode_fn_dtype<0>(dtype);
+int form_of(int reg_dv, bool stage) {
+    if (kRegDV > 0 && reg_dv == kRegDV) return stage ? 2 : 1;
+    return 0;
 }
 
-template <int DV>
+const void *decode_fn_for(int dtype, int form) {
+    if constexpr (kRegDV > 0) {
+        if (form == 2) return decode_fn_dtype<kRegDV, true>(dtype);
+        if (form == 1) return decode_fn_dtype<kRegDV, false>(dtype);
+    }
+    return decode_fn_dtype<0, false>(dtype);
+}
+
+template <int DV, bool STAGE>
 cudaError_t launch_dv(int dtype, const DecodeArgs &a, const LaunchCfg &lc) {
     switch (dtype) {
-        case 0: decode_kernel<kD, kL, DV, float, kMaxT><<<lc.grid, lc.block, lc.smem, lc.stream>>>(a); break;
-        case 1: decode_kernel<kD, kL, DV, __nv_bfloat16, kMaxT><<<lc.grid, lc.block, lc.smem, lc.stream>>>(a); break;
-        case 2: decode_kernel<kD, kL, DV, __half, kMaxT><<<lc.grid, lc.block, lc.smem, lc.stream>>>(a); break;
+        case 0: decode_kernel<kD, kL, DV, float, kMaxT, STAGE><<<lc.grid, lc.block, lc.smem, lc.stream>>>(a); break;
+        case 1: decode_kernel<kD, kL, DV, __nv_bfloat16, kMaxT, STAGE><<<lc.grid, lc.block, lc.smem, lc.stream>>>(a); break;
+        case 2: decode_kernel<kD, kL, DV, __half, kMaxT, STAGE><<<lc.grid, lc.block, lc.smem, lc.stream>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -54,19 +66,20 @@ cudaError_t launch_dv(int dtype, const DecodeArgs &a, const LaunchCfg &lc) {
 }  // namespace
 
 // Largest dynamic shared memory already granted to each kernel of this class
-// ([dtype][regular form]); the attribute is set only when a launch needs more,
-// so decodes in a steady state (and under CUDA-graph capture) make no
-// attribute calls.  Per device: a kernel attribute is per device.
-static std::atomic<int> g_smem_granted[64][3][2];
+// ([dtype][form]); the attribute is set only when a launch needs more, so
+// decodes in a steady state (and under CUDA-graph capture) make no attribute
+// calls.  Per device: a kernel attribute is per device.
+static std::atomic<int> g_smem_granted[64][3][kForms];
 
-cudaError_t LPDEC_CAT(prepare_decode_, LPDEC_D)(int dtype, int reg_dv, size_t smem) {
-    const void *fn = decode_fn_for(dtype, reg_dv);
+cudaError_t LPDEC_CAT(prepare_decode_, LPDEC_D)(int dtype, int reg_dv, bool stage, size_t smem) {
+    const int form = form_of(reg_dv, stage);
+    const void *fn = decode_fn_for(dtype, form);
     if (!fn) return cudaErrorInvalidValue;
     int dev = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return err;
     if (dev < 0 || dev >= 64) return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    std::atomic<int> &granted = g_smem_granted[dev][dtype][(kRegDV > 0 && reg_dv == kRegDV) ? 1 : 0];
+    std::atomic<int> &granted = g_smem_granted[dev][dtype][form];
     if ((int)smem <= granted.load()) return cudaSuccess;
     err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err == cudaSuccess) {
@@ -77,17 +90,21 @@ cudaError_t LPDEC_CAT(prepare_decode_, LPDEC_D)(int dtype, int reg_dv, size_t sm
     return err;
 }
 
-cudaError_t LPDEC_CAT(occupancy_decode_, LPDEC_D)(int dtype, int reg_dv, int block, size_t smem,
+cudaError_t LPDEC_CAT(occupancy_decode_, LPDEC_D)(int dtype, int reg_dv, bool stage, int block, size_t smem,
                                                    int *blocks_per_sm) {
-    const void *fn = decode_fn_for(dtype, reg_dv);
+    const void *fn = decode_fn_for(dtype, form_of(reg_dv, stage));
     if (!fn) return cudaErrorInvalidValue;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem);
 }
 
 cudaError_t LPDEC_CAT(launch_decode_, LPDEC_D)(int dtype, int reg_dv, const DecodeArgs &a, const LaunchCfg &lc) {
     if (lc.block > kMaxT) return cudaErrorInvalidConfiguration;
-    if (kRegDV > 0 && reg_dv == kRegDV) return launch_dv<kRegDV>(dtype, a, lc);
-    return launch_dv<0>(dtype, a, lc);
+    if constexpr (kRegDV > 0) {
+        const int form = form_of(reg_dv, a.slice_base > 0);
+        if (form == 2) return launch_dv<kRegDV, true>(dtype, a, lc);
+        if (form == 1) return launch_dv<kRegDV, false>(dtype, a, lc);
+    }
+    return launch_dv<0, false>(dtype, a, lc);
 }
 
 cudaError_t LPDEC_CAT(launch_project_, LPDEC_D)(int d, long long count, const float *v, float *z,

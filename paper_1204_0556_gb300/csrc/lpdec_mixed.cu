@@ -41,8 +41,8 @@ __device__ __noinline__ void mixed_round(const MixedCode *mc, MixedIO b, unsigne
     const int bar = 1 + g;
     unsigned char *base = smem_raw + (size_t)g * mc->smem_per_group;
     Slice<S> sm;
-    sm.z = reinterpret_cast<S *>(base);
-    sm.l = sm.z + mc->view.Ep;
+    sm.w = reinterpret_cast<S *>(base);
+    sm.l = sm.w + mc->view.Ep;
     sm.x = reinterpret_cast<float *>(base + mc->off_x);
     sm.red = reinterpret_cast<float *>(base + mc->off_red);
     sm.flags = reinterpret_cast<int *>(sm.red + 2 * (T >> 5));
@@ -63,7 +63,7 @@ __device__ __noinline__ void mixed_round(const MixedCode *mc, MixedIO b, unsigne
         io.bits = b.bits_out ? b.bits_out + off : nullptr;
         io.iters = b.iters_out ? b.iters_out + f : nullptr;
         io.cert = b.cert_out ? b.cert_out + f : nullptr;
-        io.z_state = io.l_state = nullptr;
+        io.w_state = io.l_state = nullptr;
         io.k_state = nullptr;
         frame_run<D, L, DV, S>(mc->view, mc->cfg, mc->cfg.max_iter, io, sm, t, T, bar, phase);
     }

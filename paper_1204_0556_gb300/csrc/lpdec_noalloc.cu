@@ -2,7 +2,7 @@
 // device memory while they run.
 //
 // lpdec_decode takes its scratch space (work-queue counters and, for the
-// STREAMED schedule, the parked z/lambda state) from cudaMallocAsync on every
+// STREAMED schedule, the parked w/lambda state) from cudaMallocAsync on every
 // call.  Some callers cannot do that: a receive loop with a fixed memory
 // footprint and a latency budget that rules out allocator calls, or a host
 // framework that owns all device memory through its own allocator and forbids

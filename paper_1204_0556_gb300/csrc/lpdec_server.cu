@@ -1,7 +1,7 @@
 // Continuous-batching decode server (lpdec_server_*).
 //
 // Each code added to the server owns a pool of frame slots in device memory:
-// LLRs, x/bits/iteration/certificate outputs and the parked z and lambda/mu
+// LLRs, x/bits/iteration/certificate outputs and the parked w = z - lambda/mu and lambda/mu
 // state of every frame in flight.  A scheduler thread repeats rounds:
 //   1. admit pending frames (FIFO over requests) into free slots of their
 //      code: one pinned host->device copy of the new LLR rows and a scatter
@@ -291,7 +291,7 @@ int run_round(lpdec_server *sv) {
         a.bits_out = P.bits;
         a.iters_out = P.iters;
         a.cert_out = P.cert;
-        a.z_state = P.zst;
+        a.w_state = P.zst;
         a.l_state = P.lst;
         a.k_state = P.kst;
         a.iters_this_launch = P.params.iters_per_launch;
