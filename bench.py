@@ -156,10 +156,10 @@ def algorithmic_ops_per_frame_iter(code) -> int:
 KERNEL_SOURCES = ("lpdec_device.cuh", "lpdec_kclass.cuh", "lpdec_internal.h")
 MEASURED_TRAFFIC = {
     # "code/schedule": (source hash, bytes per frame per launch, capture)
-    "C1056/resident": ("00771f58f322f23b", (33_898_496 + 1_631_744) / 8000,
+    "C1056/resident": ("3ccf32cee5bce70f", (33_859_584 + 2_085_888) / 8000,
                  "profiles/decode_kernel_resident_C1056_small.md: 8000 frames x 300 iterations in one launch (tile 128 x 2)"),
-    "C1056/streamed": ("d32fd46792611e22", (236_679_936 + 141_560_320) / 8000,
-                 "profiles/decode_kernel_streamed_C1056_small.md: one iteration of 8000 frames per launch"),
+    "C1056/streamed": ("3ccf32cee5bce70f", (236_629_248 + 141_584_384) / 8000,
+                 "profiles/decode_kernel_streamed_C1056_small.md: one iteration of 8000 frames per launch (tile 128 x 2)"),
 }
 
 
@@ -310,13 +310,18 @@ def _time_call(fn, steps, warmup):
     return e0.elapsed_time(e1) / steps
 
 
+# Autotuner sample: enough frames for about 20 rounds of the frames a persistent
+# grid holds in flight, so that tail effects of a short sample do not pick the tile.
+AUTOTUNE_FRAMES = 16384
+
+
 def autotune_codes(lpdec, handles, llrs, state):
-    """Pick each code's tile with lpdec_autotune on up to 2048 of its frames (60 fixed iterations)."""
+    """Pick each code's tile with lpdec_autotune on up to 16384 of its frames (60 fixed iterations)."""
     import torch
 
     tiles = []
     for C, llr in zip(handles, llrs):
-        sample = torch.from_numpy(np.ascontiguousarray(llr[:2048])).cuda()
+        sample = torch.from_numpy(np.ascontiguousarray(llr[:AUTOTUNE_FRAMES])).cuda()
         p = lpdec.make_params(mu=MU, rho=RHO, eps=0.0, max_iter=60, state=state, schedule="resident")
         tiles.append(lpdec.lpdec_autotune(C.handle, p, sample.shape[0], sample.data_ptr(),
                                           int(torch.cuda.current_stream().cuda_stream)))
@@ -728,7 +733,7 @@ def main():
         lpdec.lpdec_set_tile(C.handle, {"f32": 0, "bf16": 1, "f16": 2}[args.state], gt, g)
         tile = {"group_threads": gt, "groups": g, "source": "--tile"}
     elif not args.no_autotune:
-        sample = torch.from_numpy(np.ascontiguousarray(llr_h[:: max(1, F // 2048)][:2048])).cuda()
+        sample = torch.from_numpy(np.ascontiguousarray(llr_h[:: max(1, F // AUTOTUNE_FRAMES)][:AUTOTUNE_FRAMES])).cuda()
         tile = lpdec.lpdec_autotune(C.handle, lpdec.make_params(mu=MU, rho=RHO, eps=0.0, max_iter=60,
                                                                  state=args.state, schedule="resident"),
                                     sample.shape[0], sample.data_ptr(), int(torch.cuda.current_stream().cuda_stream))

@@ -23,6 +23,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace lpdec {
 
 constexpr float kPadV = -1.0e30f;  // value of an unused lane of a check (clips to 0)
@@ -298,6 +300,12 @@ __device__ __forceinline__ float warp_max(float v) {
 // DV > 0: the code is regular (every check has degree D, so check j owns
 // edges j*D .. j*D+D-1, and every variable has degree DV); the edge state of a
 // check is then read and written in aligned pairs.
+// The regular form with FP32 state folds x into the edge state in iterations
+// without residuals (see frame_run); 16-bit state would round
+// u = rho x + (1 - rho) w, so it gathers x.
+template <typename S>
+constexpr bool kFoldX = std::is_same<S, float>::value;
+
 // RES: also accumulate the primal and dual residual terms (iterations that run
 // the stopping test or produce the certificate); without them z_old is not
 // needed and v = rho x + (1 - rho) w + (2 - rho) lambda/mu directly.
@@ -315,10 +323,15 @@ __device__ __forceinline__ void check_update(const CodeView &c, const IterCfg &p
         const uint32_t *ci = reinterpret_cast<const uint32_t *>(c.col16 + e0);
 #pragma unroll
         for (int k = 0; k < D; k += 2) {
+            const float2 w2 = ld2<S>(ws + e0 + k);  // u = rho x + (1 - rho) w when folded
+            const float2 l2 = ld2<S>(ls + e0 + k);
+            if constexpr (!RES && kFoldX<S>) {  // regular form (kPairs): ws holds u
+                v[k] = fmaf(p.tmr, l2.x, w2.x);
+                v[k + 1] = fmaf(p.tmr, l2.y, w2.y);
+                continue;
+            }
             const uint32_t cc = ci[k / 2];
             const float x0 = xs[cc & 0xffffu], x1 = xs[cc >> 16];
-            const float2 w2 = ld2<S>(ws + e0 + k);
-            const float2 l2 = ld2<S>(ls + e0 + k);
             if constexpr (RES) {
                 const float z0 = w2.x + l2.x, z1 = w2.y + l2.y;  // z_old
                 if constexpr (kKeep) { xv[k] = x0; xv[k + 1] = x1; zo[k] = z0; zo[k + 1] = z1; }
@@ -334,8 +347,8 @@ __device__ __forceinline__ void check_update(const CodeView &c, const IterCfg &p
         for (int k = 0; k < D; ++k) {
             if (k < d) {
                 const int e = e0 + k;
-                const float xk = xs[__ldg(c.col_idx + e)];
                 const float lk = ld<S>(ls[e]);
+                const float xk = xs[__ldg(c.col_idx + e)];
                 if constexpr (RES) {
                     const float zk = ld<S>(ws[e]) + lk;  // z_j^old
                     if constexpr (kKeep) { xv[k] = xk; zo[k] = zk; }
@@ -409,10 +422,22 @@ __device__ __forceinline__ int seg_sum_i(int x) {
     return x;
 }
 
+template <int L>
+__device__ __forceinline__ int seg_min_i(int x) {
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1) x = min(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+
+// v = rho x + (1 - rho) w + (2 - rho) lambda/mu (z_old is not formed); when
+// need_res, the residual terms re-read the old w and lambda/mu before they are
+// overwritten.  (One instantiation with a runtime flag: two inlined copies of
+// this update exceed the 64-register budget of the 1024-thread kernel.)
 template <int D, int L, typename S>
 __device__ __forceinline__ void check_update_seg(const CodeView &c, const IterCfg &p, int j, bool valid,
                                                  S *ws, S *ls, const float *xs, bool need_res,
                                                  float &rp, float &rd) {
+    static_assert(D <= 32, "packed facet keys hold a 5-bit entry index");
     constexpr int V = (D + L - 1) / L;
     const int r = threadIdx.x & (L - 1);
     int e0 = 0, d = 0;
@@ -427,42 +452,37 @@ __device__ __forceinline__ void check_update_seg(const CodeView &c, const IterCf
         if (q < d) {
             const int e = e0 + q;
             const float xk = xs[__ldg(c.col_idx + e)];
-            const float lk = ld<S>(ls[e]);
-            const float zk = ld<S>(ws[e]) + lk;  // z_old
-            v[k] = fmaf(p.rho, xk, p.omr * zk) + lk;
+            v[k] = fmaf(p.rho, xk, fmaf(p.omr, ld<S>(ws[e]), p.tmr * ld<S>(ls[e])));
         } else {
             v[k] = kPadV;
         }
     }
-    // facet: S = {zh > 1/2}, flip the entry closest to 1/2 when |S| is even
+    // facet: S = {zh > 1/2}, flip the entry closest to 1/2 when |S| is even;
+    // violation test sum_k |zh_k - 1/2| (- 2 min when flipped) > d/2 - 1, with
+    // the packed argmin key of project_pp, reduced over the segment.
     unsigned th = 0u;
-    float best = 2.0f;
-    int kb = 1 << 30;
+    int key = 0x7fffffff;
+    float sdist = 0.0f;
 #pragma unroll
     for (int k = 0; k < V; ++k) {
         const float zh = __saturatef(v[k]);
         if (zh > 0.5f) th |= 1u << k;
         const float dist = fabsf(zh - 0.5f);
         const int q = k * L + r;
-        if (q < d && dist < best) { best = dist; kb = q; }
+        if (q < d) {
+            sdist += dist;
+            key = min(key, (__float_as_int(dist) & ~31) | q);
+        }
     }
-#pragma unroll
-    for (int o = 1; o < L; o <<= 1) {
-        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int ok = __shfl_xor_sync(0xffffffffu, kb, o);
-        if (ob < best || (ob == best && ok < kb)) { best = ob; kb = ok; }
-    }
+    key = seg_min_i<L>(key);
+    sdist = seg_sum<L>(sdist);
     const int s = seg_sum_i<L>(__popc(th));
-    if ((s & 1) == 0 && kb < d && (kb % L) == r) th ^= 1u << (kb / L);
-    const int ssz = seg_sum_i<L>(__popc(th));  // |S|, odd
-    float g = 0.0f;
-#pragma unroll
-    for (int k = 0; k < V; ++k) {
-        const float zh = __saturatef(v[k]);
-        g += ((th >> k) & 1u) ? zh : -zh;
+    if ((s & 1) == 0 && d > 0) {
+        const int kb = key & 31;
+        if ((kb % L) == r) th ^= 1u << (kb / L);
+        sdist -= 2.0f * __int_as_float(key & ~31);
     }
-    g = seg_sum<L>(g);
-    const bool violated = d > 0 && g > (float)(ssz - 1);  // else zh is the projection
+    const bool violated = d > 0 && sdist > 0.5f * (float)d - 1.0f;  // else zh is the projection
     float beta = 0.0f;
     {
         // fixed point of sum_k max(0, beta - kappa_k) = 1, from all entries active
@@ -685,6 +705,15 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
     const int k_end = min(p.max_iter, k + iters_this_launch);
     bool conv = false, rok = false;
     while (k < k_end) {
+        // Residual terms are needed by the stopping test and, on the last
+        // iteration, by the certificate.
+        const bool need_res = p.check_stop || (k + 1 == p.max_iter);
+        // Regular form with FP32 state, iterations without residuals: after
+        // computing x_i the variable thread folds it into its edges,
+        // overwriting w_e with u_e = rho x_i + (1 - rho) w_e, so the check
+        // update forms v = u + (2 - rho) lambda/mu without gathering x.  (The
+        // generic form would need a second pass over each variable's edges.)
+        const bool fold = kFoldX<S> && DV > 0 && !need_res;
         // ---- x-update (Algorithm 1; Section 3.2): sum over the edges of w = z - lambda/mu
         for (int i = t; i < c.n; i += T) {
             float acc = 0.0f, inv_dv;
@@ -692,9 +721,20 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
                 static_assert(DV <= 4, "regular form holds up to 4 edges per variable");
                 const uint2 pk = *reinterpret_cast<const uint2 *>(c.csc16 + 4 * i);
                 const unsigned es[4] = {pk.x & 0xffffu, pk.x >> 16, pk.y & 0xffffu, pk.y >> 16};
+                float wv[DV];
 #pragma unroll
-                for (int s = 0; s < DV; ++s) acc += ld<S>(sm.w[es[s]]);
+                for (int s = 0; s < DV; ++s) {
+                    wv[s] = ld<S>(sm.w[es[s]]);
+                    acc += wv[s];
+                }
                 inv_dv = 1.0f / (float)DV;
+                const float gi = __ldg(gam + i);
+                const float x = __saturatef((acc - gi * p.mu_inv) * inv_dv);
+                sm.x[i] = x;
+                if (fold) {
+#pragma unroll
+                    for (int s = 0; s < DV; ++s) sm.w[es[s]] = st<S>(fmaf(p.rho, x, p.omr * wv[s]));
+                }
             } else {
                 const int s0 = __ldg(c.col_ptr + i), s1 = __ldg(c.col_ptr + i + 1);
                 for (int s = s0; s < s1; ++s) {
@@ -702,13 +742,13 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
                     acc += ld<S>(sm.w[e]);
                 }
                 inv_dv = __frcp_rn((float)(s1 - s0));
+                const float gi = __ldg(gam + i);
+                const float x = __saturatef((acc - gi * p.mu_inv) * inv_dv);
+                sm.x[i] = x;
             }
-            const float gi = __ldg(gam + i);
-            sm.x[i] = __saturatef((acc - gi * p.mu_inv) * inv_dv);
         }
         group_sync(bar, T);
         // ---- z- and lambda-updates (Algorithm 1; Section 5.2 over-relaxation)
-        const bool need_res = p.check_stop || (k + 1 == p.max_iter);
         float rp = 0.0f, rd = 0.0f;
         if constexpr (L == 1) {
             if (need_res) {

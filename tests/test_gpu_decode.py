@@ -289,6 +289,34 @@ def test_autotune_keeps_results(gpu, c1056):
         C.close()
 
 
+@pytest.mark.parametrize("state", ["f32", "bf16"])
+@pytest.mark.parametrize("eps", [0.0, 1e-5])
+def test_staged_and_global_index_forms_agree(gpu, c1056, state, eps):
+    """The regular-code kernel reads the code's 16-bit indices from a copy in
+    shared memory when it fits beside the frame slices, else from global
+    memory.  C1056 slices are 29,696 B (FP32) and 17,024 B (BF16) for 64-thread
+    groups and the index block takes 14,848 B, so with 227 KB of shared memory
+    7 FP32 or 12 BF16 groups stage it and 13 BF16 groups do not.  Every tile
+    with the same group width must give identical outputs."""
+    import torch
+
+    llr = I.awgn_llr(c1056, 2.0, 96, 909)
+    C = gpu.Code(c1056)
+    try:
+        d_llr = torch.from_numpy(llr).cuda()
+        p = gpu.make_params(eps=eps, max_iter=150, state=state)
+        dt = {"f32": 0, "bf16": 1}[state]
+        outs = []
+        for g in ((1, 7) if state == "f32" else (1, 12, 13)):
+            gpu.lpdec_set_tile(C.handle, dt, 64, g)
+            outs.append({k: v.cpu().numpy() for k, v in gpu.decode(C, d_llr, p).items()})
+        for o in outs[1:]:
+            for k in ("x", "bits", "iters", "cert"):
+                assert np.array_equal(outs[0][k], o[k]), k
+    finally:
+        C.close()
+
+
 @pytest.mark.parametrize("mu,rho", [(1.0, 1.0), (7.0, 1.5), (3.0, 1.99)])
 def test_other_penalties_and_relaxations(gpu, oracle_mod, c96, mu, rho):
     llr = I.awgn_llr(c96, 2.0, 40, 21)
