@@ -732,11 +732,23 @@ def main():
         gt, g = (int(v) for v in args.tile.split(","))
         lpdec.lpdec_set_tile(C.handle, {"f32": 0, "bf16": 1, "f16": 2}[args.state], gt, g)
         tile = {"group_threads": gt, "groups": g, "source": "--tile"}
-    elif not args.no_autotune:
-        sample = torch.from_numpy(np.ascontiguousarray(llr_h[:: max(1, F // AUTOTUNE_FRAMES)][:AUTOTUNE_FRAMES])).cuda()
-        tile = lpdec.lpdec_autotune(C.handle, lpdec.make_params(mu=MU, rho=RHO, eps=0.0, max_iter=60,
-                                                                 state=args.state, schedule="resident"),
-                                    sample.shape[0], sample.data_ptr(), int(torch.cuda.current_stream().cuda_stream))
+    tune_sample = []
+
+    def tune(schedule, state):
+        """Autotune the tile of one (schedule, state) on a sample of the workload:
+        60 fixed iterations for RESIDENT, 6 launches for STREAMED."""
+        if not tune_sample:
+            tune_sample.append(torch.from_numpy(
+                np.ascontiguousarray(llr_h[:: max(1, F // AUTOTUNE_FRAMES)][:AUTOTUNE_FRAMES])).cuda())
+        smp = tune_sample[0]
+        sch = "streamed" if schedule == "streamed" else "resident"
+        p = lpdec.make_params(mu=MU, rho=RHO, eps=0.0, max_iter=6 if sch == "streamed" else 60, state=state,
+                              schedule=sch)
+        return lpdec.lpdec_autotune(C.handle, p, smp.shape[0], smp.data_ptr(),
+                                    int(torch.cuda.current_stream().cuda_stream))
+
+    if not args.tile and not args.no_autotune:
+        tile = tune(args.schedule, args.state)
     dev = torch.device("cuda", local)
     llr = torch.from_numpy(llr_h).to(dev)
     out = {
@@ -838,12 +850,16 @@ def main():
         for sch, st in (("streamed", "f32"), ("streamed", "bf16"), ("resident", "bf16")):
             if (sch, st) == (args.schedule, args.state):
                 continue
+            vtile = None
+            if not args.tile and not args.no_autotune:
+                vtile = tune(sch, st)
             vms = time_variant(sch, st, max(2, args.steps // 2), 2)
             vb = algorithmic_bytes_per_frame_iter(code, 4 if st == "f32" else 2)
             vl = 1 if sch == "resident" else ITERS
             vach = F * (ITERS // vl) * vb / ((vms / vl) / 1000.0) / 1e9
             var[f"{sch}-{st}"] = {"value": F * code.k_design / (vms / 1000.0), "ms_per_step": vms,
-                                  "hbm_frac": round(vach / hbm_peak, 4), "launches_per_step": vl}
+                                  "hbm_frac": round(vach / hbm_peak, 4), "launches_per_step": vl,
+                                  "tile": vtile}
         line["variants"] = var
 
     if not args.no_e2e:

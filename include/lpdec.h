@@ -132,16 +132,21 @@ LPDEC_API int lpdec_code_destroy(lpdec_code *code);
  * Autotuner: time the candidate tiles of a code (frames decoded at once per
  * CTA x threads per frame, within the register, barrier and shared-memory
  * limits) on the caller's sample of n_frames frames (llr: device pointer
- * [n_frames x n]) with params (RESIDENT schedule), keep the fastest for that
- * state dtype in the code object, and report it.  Later decodes of the code
- * (lpdec_decode, lpdec_decode_mixed, the server) use the tuned tile.
+ * [n_frames x n]) with params, keep the fastest for that state dtype and
+ * schedule in the code object, and report it.  params.schedule = STREAMED
+ * tunes the STREAMED tile (with params.max_iter launches per candidate, so a
+ * few iterations suffice); RESIDENT or AUTO tunes the RESIDENT tile.  Later
+ * decodes of the code use the tile of their schedule (STREAMED decodes fall
+ * back to the RESIDENT tile when no STREAMED tile was tuned); the server and
+ * lpdec_decode_mixed use the RESIDENT tile.
  * Synchronizes cuda_stream.  Any output pointer may be NULL.
  */
 LPDEC_API int lpdec_autotune(lpdec_code *code, const lpdec_params *params, int32_t n_frames, const float *llr,
                              void *cuda_stream, int32_t *group_threads, int32_t *groups, double *ms_per_frame);
 
-/* Set a code's tile for one state dtype by hand (groups x group_threads);
- * 0, 0 restores the built-in default.  LPDEC_EINVAL for a tile that does not fit. */
+/* Set a code's tile for one state dtype by hand (groups x group_threads), for
+ * both schedules; 0, 0 restores the built-in default.  LPDEC_EINVAL for a tile
+ * that does not fit. */
 LPDEC_API int lpdec_set_tile(lpdec_code *code, int32_t state_dtype, int32_t group_threads, int32_t groups);
 
 /* ---- decoding ---------------------------------------------------------- */

@@ -144,14 +144,20 @@ extern "C" int lpdec_code_create(int32_t n, int32_t m, const int32_t *row_ptr, c
     c->max_dc = max_dc;
     c->k_rank = gf2_k_rank(n, m, row_ptr, col_idx);
     c->cls = lpdec::degree_class(max_dc);
-    // Regular code whose check degree is exactly its class width: the decode
-    // kernel can then take edge offsets from j*D and i*DV.
+    // Regular codes (one check degree, one variable degree) run the regular-code
+    // kernel, which takes edge offsets from j*dc and i*dv: (3,6)-type codes in
+    // the class D = 6, (4,8) in D = 8 (check degree equal to the class width),
+    // and degree-3 variables with any check degree in the wide classes.
     {
+        const int dc0 = row_ptr[1] - row_ptr[0], dv0 = col_ptr[1] - col_ptr[0];
         bool reg = true;
-        const int dv0 = col_ptr[1] - col_ptr[0];
-        for (int j = 0; j < m && reg; ++j) reg = (row_ptr[j + 1] - row_ptr[j]) == lpdec::kClassD[c->cls];
+        for (int j = 0; j < m && reg; ++j) reg = (row_ptr[j + 1] - row_ptr[j]) == dc0;
         for (int i = 0; i < n && reg; ++i) reg = (col_ptr[i + 1] - col_ptr[i]) == dv0;
+        const int D = lpdec::kClassD[c->cls];
+        const int want_dv = D == 8 ? 4 : 3;
+        reg = reg && dv0 == want_dv && (D > 8 || dc0 == D);
         c->reg_dv = reg ? dv0 : 0;
+        c->reg_dc = reg ? dc0 : 0;
     }
     cudaError_t err = cudaGetDevice(&c->device);
     if (err != cudaSuccess) { delete c; return cuda_error(err, "lpdec_code_create: cudaGetDevice"); }
@@ -179,7 +185,7 @@ extern "C" int lpdec_code_create(int32_t n, int32_t m, const int32_t *row_ptr, c
     }
     // Regular codes: 16-bit index block for the regular-form kernels.  Codes
     // whose indices need more than 16 bits run the generic form instead.
-    if (c->reg_dv > 0 && (E > 65535 || n > 65535 || c->reg_dv > 4)) c->reg_dv = 0;
+    if (c->reg_dv > 0 && (E > 65535 || n > 65535 || c->reg_dv > 4)) c->reg_dv = c->reg_dc = 0;
     if (c->reg_dv > 0) {
         c->col16_elems = (int)((E + 7) / 8 * 8);
         c->idx16_bytes = (int)((size_t)c->col16_elems * 2 + (((size_t)n * 8 + 15) & ~(size_t)15));  // copy16 moves 16-byte units
@@ -322,6 +328,13 @@ Tile default_tile(const lpdec_code *c, int dtype, int max_threads) {
     return t;
 }
 
+Tile chosen_tile(const lpdec_code *c, const lpdec_params *p) {
+    const int dt = p->state_dtype;
+    if (p->schedule == LPDEC_SCHED_STREAMED && c->tuned_streamed[dt].valid) return c->tuned_streamed[dt];
+    if (c->tuned[dt].valid) return c->tuned[dt];
+    return default_tile(c, dt);
+}
+
 int plan_launch(const lpdec_code *c, int dtype, const Tile &tile, int n_frames, cudaStream_t stream,
                 LaunchCfg *lc, SliceLayout *layout) {
     const SliceLayout L = slice_layout(c, dtype, tile.group_threads);
@@ -401,6 +414,7 @@ CodeView make_view(const lpdec_code *c) {
     v.csc16 = c->dev_idx16 ? v.col16 + c->col16_elems : nullptr;
     v.idx16_bytes = c->idx16_bytes;
     v.col16_elems = c->col16_elems;
+    v.reg_dc = c->reg_dc;
     return v;
 }
 
@@ -503,7 +517,7 @@ extern "C" int lpdec_decode(const lpdec_code *c, int32_t n_frames, const float *
     if (n_frames == 0) return LPDEC_OK;
     if (!llr || !x_out) return set_error(LPDEC_EINVAL, "lpdec_decode: llr and x_out must not be NULL");
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
-    const lpdec::Tile tile = c->tuned[p->state_dtype].valid ? c->tuned[p->state_dtype] : lpdec::default_tile(c, p->state_dtype);
+    const lpdec::Tile tile = lpdec::chosen_tile(c, p);
     const int schedule = lpdec::resolve_schedule(c, p, tile);
     const size_t wb = lpdec::workspace_bytes(c, n_frames, schedule, p->state_dtype, p->max_iter, p->iters_per_launch);
     void *work = nullptr;
@@ -572,7 +586,8 @@ extern "C" int lpdec_autotune(lpdec_code *c, const lpdec_params *p, int32_t n_fr
     if (rc) return rc;
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
     lpdec_params q = *p;
-    q.schedule = LPDEC_SCHED_RESIDENT;
+    const bool streamed = p->schedule == LPDEC_SCHED_STREAMED;
+    if (!streamed) q.schedule = LPDEC_SCHED_RESIDENT;
     const int lanes = lpdec::class_lanes(lpdec::kClassD[c->cls]);
     const int maxT = lpdec::class_max_threads(c->cls);
     const int cap = lpdec::device_smem_optin(c->device);
@@ -595,7 +610,7 @@ extern "C" int lpdec_autotune(lpdec_code *c, const lpdec_params *p, int32_t n_fr
     if (cand.empty()) return set_error(LPDEC_EINVAL, "lpdec_autotune: no tile fits this code");
     const size_t nx = (size_t)n_frames * c->n;
     char *buf = nullptr;
-    const size_t wb = lpdec::workspace_bytes(c, n_frames, LPDEC_SCHED_RESIDENT, q.state_dtype, q.max_iter, 1);
+    const size_t wb = lpdec::workspace_bytes(c, n_frames, q.schedule, q.state_dtype, q.max_iter, q.iters_per_launch);
     cudaError_t err = cudaMallocAsync(reinterpret_cast<void **>(&buf), nx * 4 + 256 + wb, stream);
     if (err != cudaSuccess) return cuda_error(err, "lpdec_autotune: cudaMallocAsync");
     float *x = reinterpret_cast<float *>(buf);
@@ -608,12 +623,12 @@ extern "C" int lpdec_autotune(lpdec_code *c, const lpdec_params *p, int32_t n_fr
     rc = LPDEC_OK;
     for (const auto &t : cand) {
         rc = lpdec::enqueue_decode(c, n_frames, llr, &q, x, nullptr, nullptr, nullptr, stream, work,
-                                   LPDEC_SCHED_RESIDENT, t, nullptr);  // warm-up
+                                   q.schedule, t, nullptr);  // warm-up
         if (rc) break;
         cudaEventRecord(e0, stream);
         for (int r = 0; r < 2 && !rc; ++r)
             rc = lpdec::enqueue_decode(c, n_frames, llr, &q, x, nullptr, nullptr, nullptr, stream, work,
-                                       LPDEC_SCHED_RESIDENT, t, nullptr);
+                                       q.schedule, t, nullptr);
         cudaEventRecord(e1, stream);
         if (rc) break;
         err = cudaEventSynchronize(e1);
@@ -629,7 +644,7 @@ extern "C" int lpdec_autotune(lpdec_code *c, const lpdec_params *p, int32_t n_fr
     cudaStreamSynchronize(stream);
     if (rc) return rc;
     best_t.valid = true;
-    c->tuned[q.state_dtype] = best_t;
+    (streamed ? c->tuned_streamed : c->tuned)[q.state_dtype] = best_t;
     if (group_threads_out) *group_threads_out = best_t.group_threads;
     if (groups_out) *groups_out = best_t.groups;
     if (ms_per_frame_out) *ms_per_frame_out = best;
@@ -641,6 +656,7 @@ extern "C" int lpdec_set_tile(lpdec_code *c, int32_t state_dtype, int32_t group_
     if (state_dtype < 0 || state_dtype > 2) return set_error(LPDEC_EINVAL, "lpdec_set_tile: unknown state_dtype");
     if (group_threads == 0 && groups == 0) {  // back to the built-in default
         c->tuned[state_dtype] = lpdec::Tile();
+        c->tuned_streamed[state_dtype] = lpdec::Tile();
         return LPDEC_OK;
     }
     const int maxT = lpdec::class_max_threads(c->cls);
@@ -655,6 +671,7 @@ extern "C" int lpdec_set_tile(lpdec_code *c, int32_t state_dtype, int32_t group_
     t.groups = groups;
     t.valid = true;
     c->tuned[state_dtype] = t;
+    c->tuned_streamed[state_dtype] = t;
     return LPDEC_OK;
 }
 

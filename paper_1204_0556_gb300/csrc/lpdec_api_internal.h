@@ -30,6 +30,9 @@ CodeView make_view(const lpdec_code *c);
 SliceLayout slice_layout(const lpdec_code *c, int dtype, int group_threads);
 // max_threads > 0 caps the CTA size (kernels built for smaller CTAs).
 Tile default_tile(const lpdec_code *c, int dtype, int max_threads = 0);
+// The tile a decode with these parameters uses: the tuned tile of its schedule
+// (STREAMED has its own), else the RESIDENT one, else the default.
+Tile chosen_tile(const lpdec_code *c, const lpdec_params *p);
 int device_smem_optin(int device);
 int device_sm_count(int device);
 int plan_launch(const lpdec_code *c, int dtype, const Tile &tile, int n_frames, cudaStream_t stream,
@@ -46,12 +49,14 @@ int enqueue_decode(const lpdec_code *c, int n_frames, const float *llr, const lp
 struct lpdec_code {
     int n = 0, m = 0, E = 0, Ep = 0;
     int max_dc = 0, k_rank = 0, cls = 0, device = 0;
-    int reg_dv = 0;             // variable degree if the code is regular with check degree == class D, else 0
+    int reg_dv = 0;             // variable degree if the code runs the regular-code kernel, else 0
+    int reg_dc = 0;             // the common check degree of such a code
     void *dev_block = nullptr;  // one allocation holding the four index arrays
     int32_t *row_ptr = nullptr, *col_idx = nullptr, *col_ptr = nullptr, *csc_edge = nullptr;
     // Regular codes: 16-bit index block (CodeView::col16 / csc16), else null.
     void *dev_idx16 = nullptr;
     int idx16_bytes = 0, col16_elems = 0;
-    lpdec::Tile tuned[3];  // per state dtype, from lpdec_autotune
+    lpdec::Tile tuned[3];           // per state dtype, from lpdec_autotune (RESIDENT) or lpdec_set_tile
+    lpdec::Tile tuned_streamed[3];  // per state dtype, from lpdec_autotune (STREAMED) or lpdec_set_tile
     lpdec::Tile dual_tile;  // tile of the dual subgradient decoder, from lpdec_dual_set_tile
 };

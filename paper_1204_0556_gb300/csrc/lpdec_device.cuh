@@ -237,6 +237,7 @@ struct CodeView {
     const uint16_t *csc16;
     int idx16_bytes;
     int col16_elems;
+    int reg_dc;               // regular codes: the common check degree (check j owns edges j*reg_dc ...)
 };
 
 struct IterCfg {
@@ -433,7 +434,10 @@ __device__ __forceinline__ int seg_min_i(int x) {
 // need_res, the residual terms re-read the old w and lambda/mu before they are
 // overwritten.  (One instantiation with a runtime flag: two inlined copies of
 // this update exceed the 64-register budget of the 1024-thread kernel.)
-template <int D, int L, typename S>
+// DV > 0: regular code (every check has degree c.reg_dc, every variable DV):
+// edge offsets j*reg_dc, 16-bit column indices, and in iterations without
+// residuals with FP32 state ws holds u = rho x + (1 - rho) w (see frame_run).
+template <int D, int L, int DV, typename S>
 __device__ __forceinline__ void check_update_seg(const CodeView &c, const IterCfg &p, int j, bool valid,
                                                  S *ws, S *ls, const float *xs, bool need_res,
                                                  float &rp, float &rd) {
@@ -442,17 +446,31 @@ __device__ __forceinline__ void check_update_seg(const CodeView &c, const IterCf
     const int r = threadIdx.x & (L - 1);
     int e0 = 0, d = 0;
     if (valid) {
-        e0 = __ldg(c.row_ptr + j);
-        d = __ldg(c.row_ptr + j + 1) - e0;
+        if constexpr (DV > 0) {
+            d = c.reg_dc;
+            e0 = j * d;
+        } else {
+            e0 = __ldg(c.row_ptr + j);
+            d = __ldg(c.row_ptr + j + 1) - e0;
+        }
     }
+    auto col_of = [&](int e) -> int {
+        if constexpr (DV > 0) return c.col16[e];
+        else return __ldg(c.col_idx + e);
+    };
+    const bool folded = kFoldX<S> && DV > 0 && !need_res;
     float v[V];
 #pragma unroll
     for (int k = 0; k < V; ++k) {
         const int q = k * L + r;
         if (q < d) {
             const int e = e0 + q;
-            const float xk = xs[__ldg(c.col_idx + e)];
-            v[k] = fmaf(p.rho, xk, fmaf(p.omr, ld<S>(ws[e]), p.tmr * ld<S>(ls[e])));
+            if (folded) {
+                v[k] = fmaf(p.tmr, ld<S>(ls[e]), ld<S>(ws[e]));
+            } else {
+                const float xk = xs[col_of(e)];
+                v[k] = fmaf(p.rho, xk, fmaf(p.omr, ld<S>(ws[e]), p.tmr * ld<S>(ls[e])));
+            }
         } else {
             v[k] = kPadV;
         }
@@ -532,7 +550,7 @@ __device__ __forceinline__ void check_update_seg(const CodeView &c, const IterCf
             const int e = e0 + q;
             const float z = proj_z(v[k], pr, k);
             if (need_res) {
-                const float a = xs[__ldg(c.col_idx + e)] - z;
+                const float a = xs[col_of(e)] - z;
                 const float b = z - (ld<S>(ws[e]) + ld<S>(ls[e]));
                 rp = fmaf(a, a, rp);
                 rd = fmaf(b, b, rd);
@@ -760,7 +778,7 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
             const int per_pass = T / L;
             for (int j0 = 0; j0 < c.m; j0 += per_pass) {
                 const int j = j0 + t / L;
-                check_update_seg<D, L, S>(c, p, j, j < c.m, sm.w, sm.l, sm.x, need_res, rp, rd);
+                check_update_seg<D, L, DV, S>(c, p, j, j < c.m, sm.w, sm.l, sm.x, need_res, rp, rd);
             }
         }
         ++k;

@@ -18,8 +18,10 @@ namespace {
 constexpr int kD = LPDEC_D;
 constexpr int kL = class_lanes(kD);
 constexpr int kMaxT = class_max_threads_D(kD);
-// Variable degree of the regular-code kernel built for this class (0: none).
-constexpr int kRegDV = kD == 6 ? 3 : (kD == 8 ? 4 : 0);
+// Variable degree of the regular-code kernel built for this class: (3,6)-type
+// codes for D = 6, (4,8) for D = 8, and degree-3 variables with any common
+// check degree for the wide classes.
+constexpr int kRegDV = kD == 8 ? 4 : 3;
 
 // Kernel forms of this class: 0 generic, 1 regular (indices from global
 // memory), 2 regular with the indices staged in shared memory.

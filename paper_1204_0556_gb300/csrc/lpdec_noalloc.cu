@@ -59,8 +59,7 @@ extern "C" int lpdec_decode_noalloc(const lpdec_code *c, int32_t n_frames, const
     if (rc) return rc;
     if (n_frames == 0) return LPDEC_OK;
     if (!llr || !x_out) return lpdec::set_error(LPDEC_EINVAL, "lpdec_decode_noalloc: llr and x_out must not be NULL");
-    const lpdec::Tile tile =
-        c->tuned[p->state_dtype].valid ? c->tuned[p->state_dtype] : lpdec::default_tile(c, p->state_dtype);
+    const lpdec::Tile tile = lpdec::chosen_tile(c, p);
     const int schedule = lpdec::resolve_schedule(c, p, tile);
     const size_t need =
         lpdec::workspace_bytes(c, n_frames, schedule, p->state_dtype, p->max_iter, p->iters_per_launch);

@@ -175,6 +175,46 @@ def test_other_code_shapes(gpu, oracle_mod, name, frames, iters):
     assert_parity(code, got, ref, 1e-4)
 
 
+@pytest.mark.parametrize("name", ["C4000", "S12"])
+@pytest.mark.parametrize("eps,iters", [(0.0, 40), (1e-5, 120)])
+def test_wide_regular_streamed_equals_resident(gpu, name, eps, iters):
+    """Regular codes with wide checks ((3,30) and (3,12)) run the regular-code
+    kernel of the segmented classes; both schedules give identical outputs, in
+    fixed-iteration runs (x folded into the edge state) and early-exit runs."""
+    code = _shape(name)
+    llr = I.awgn_llr(code, 3.0, 10, 404)
+    a = gpu_decode(gpu, code, llr, eps=eps, max_iter=iters, schedule="resident")
+    b = gpu_decode(gpu, code, llr, eps=eps, max_iter=iters, schedule="streamed", iters_per_launch=3)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_streamed_autotune_keeps_results(gpu, c1056):
+    """Tuning the STREAMED tile changes neither the results nor the RESIDENT tile."""
+    import torch
+
+    llr = I.awgn_llr(c1056, 2.0, 256, 505)
+    C = gpu.Code(c1056)
+    try:
+        d_llr = torch.from_numpy(llr).cuda()
+        ps = gpu.make_params(eps=0.0, max_iter=30, schedule="streamed")
+        pr = gpu.make_params(eps=0.0, max_iter=30, schedule="resident")
+        a = {k: v.cpu().numpy() for k, v in gpu.decode(C, d_llr, ps).items()}
+        r0 = {k: v.cpu().numpy() for k, v in gpu.decode(C, d_llr, pr).items()}
+        sp = int(torch.cuda.current_stream().cuda_stream)
+        t = gpu.lpdec_autotune(C.handle, gpu.make_params(eps=0.0, max_iter=4, schedule="streamed"), 256,
+                               d_llr.data_ptr(), sp)
+        assert t["group_threads"] % 32 == 0 and t["groups"] >= 1
+        b = {k: v.cpu().numpy() for k, v in gpu.decode(C, d_llr, ps).items()}
+        r1 = {k: v.cpu().numpy() for k, v in gpu.decode(C, d_llr, pr).items()}
+        for k in ("x", "bits", "iters", "cert"):
+            assert np.array_equal(a[k], b[k]), k
+            assert np.array_equal(r0[k], r1[k]), k
+            assert np.array_equal(a[k], r0[k]), k
+    finally:
+        C.close()
+
+
 def test_noiseless_all_zeros(gpu, c1056):
     llr = np.full((5, c1056.n), 4.0, dtype=np.float32)
     got = gpu_decode(gpu, c1056, llr, eps=1e-5, max_iter=100)
