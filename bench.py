@@ -736,13 +736,13 @@ def main():
 
     def tune(schedule, state):
         """Autotune the tile of one (schedule, state) on a sample of the workload:
-        60 fixed iterations for RESIDENT, 6 launches for STREAMED."""
+        60 fixed iterations for RESIDENT, 12 launches for STREAMED."""
         if not tune_sample:
             tune_sample.append(torch.from_numpy(
                 np.ascontiguousarray(llr_h[:: max(1, F // AUTOTUNE_FRAMES)][:AUTOTUNE_FRAMES])).cuda())
         smp = tune_sample[0]
         sch = "streamed" if schedule == "streamed" else "resident"
-        p = lpdec.make_params(mu=MU, rho=RHO, eps=0.0, max_iter=6 if sch == "streamed" else 60, state=state,
+        p = lpdec.make_params(mu=MU, rho=RHO, eps=0.0, max_iter=12 if sch == "streamed" else 60, state=state,
                               schedule=sch)
         return lpdec.lpdec_autotune(C.handle, p, smp.shape[0], smp.data_ptr(),
                                     int(torch.cuda.current_stream().cuda_stream))

@@ -149,6 +149,17 @@ LPDEC_API int lpdec_autotune(lpdec_code *code, const lpdec_params *params, int32
  * that does not fit. */
 LPDEC_API int lpdec_set_tile(lpdec_code *code, int32_t state_dtype, int32_t group_threads, int32_t groups);
 
+/* Set a code's STREAMED tile for one state dtype by hand (the RESIDENT tile is
+ * left as it is); 0, 0 restores the fallback to the RESIDENT tile.
+ * LPDEC_EINVAL for a tile that does not fit. */
+LPDEC_API int lpdec_set_streamed_tile(lpdec_code *code, int32_t state_dtype, int32_t group_threads, int32_t groups);
+
+/* The tile a decode of this code with this state dtype and schedule
+ * (LPDEC_SCHED_*) would use now: tuned, set by hand, or the default.  Any
+ * output pointer may be NULL. */
+LPDEC_API int lpdec_get_tile(const lpdec_code *code, int32_t state_dtype, int32_t schedule, int32_t *group_threads,
+                             int32_t *groups);
+
 /* ---- decoding ---------------------------------------------------------- */
 
 /*

@@ -265,11 +265,12 @@ static cudaError_t class_launch(const lpdec_code *c, int dtype, const DecodeArgs
 
 static size_t dtype_size(int dtype) { return dtype == LPDEC_STATE_F32 ? 4 : 2; }
 
-// Byte layout of one group's shared-memory slice (must match decode_kernel).
+// Byte layout of one group's shared-memory slice (must match decode_kernel):
+// w and lambda/mu, x, the reduction scratch, and 8 ints of flags (the last two
+// hold the mbarrier of the bulk loads).
 SliceLayout slice_layout(const lpdec_code *c, int dtype, int group_threads) {
     SliceLayout L;
-    size_t off = 2 * (size_t)c->Ep * dtype_size(dtype);
-    off = (off + 15) & ~(size_t)15;
+    size_t off = (2 * (size_t)c->Ep * dtype_size(dtype) + 15) & ~(size_t)15;
     L.off_x = off;
     off += ((size_t)c->n * 4 + 15) & ~(size_t)15;
     L.off_red = off;
@@ -672,6 +673,44 @@ extern "C" int lpdec_set_tile(lpdec_code *c, int32_t state_dtype, int32_t group_
     t.valid = true;
     c->tuned[state_dtype] = t;
     c->tuned_streamed[state_dtype] = t;
+    return LPDEC_OK;
+}
+
+extern "C" int lpdec_set_streamed_tile(lpdec_code *c, int32_t state_dtype, int32_t group_threads, int32_t groups) {
+    if (!c) return set_error(LPDEC_EINVAL, "lpdec_set_streamed_tile: code is NULL");
+    if (state_dtype < 0 || state_dtype > 2) return set_error(LPDEC_EINVAL, "lpdec_set_streamed_tile: unknown state_dtype");
+    if (group_threads == 0 && groups == 0) {
+        c->tuned_streamed[state_dtype] = lpdec::Tile();
+        return LPDEC_OK;
+    }
+    const int maxT = lpdec::class_max_threads(c->cls);
+    if (group_threads < 32 || group_threads % 32 || groups < 1 || groups > 15 || group_threads * groups > maxT)
+        return set_error(LPDEC_EINVAL, "lpdec_set_streamed_tile: %d groups x %d threads is not a valid tile", groups,
+                         group_threads);
+    const lpdec::SliceLayout L = lpdec::slice_layout(c, state_dtype, group_threads);
+    if ((int)(L.bytes * groups) > lpdec::device_smem_optin(c->device))
+        return set_error(LPDEC_EINVAL, "lpdec_set_streamed_tile: %d slices of %zu bytes exceed shared memory", groups,
+                         L.bytes);
+    lpdec::Tile t;
+    t.group_threads = group_threads;
+    t.groups = groups;
+    t.valid = true;
+    c->tuned_streamed[state_dtype] = t;
+    return LPDEC_OK;
+}
+
+extern "C" int lpdec_get_tile(const lpdec_code *c, int32_t state_dtype, int32_t schedule, int32_t *group_threads,
+                              int32_t *groups) {
+    if (!c) return set_error(LPDEC_EINVAL, "lpdec_get_tile: code is NULL");
+    if (state_dtype < 0 || state_dtype > 2) return set_error(LPDEC_EINVAL, "lpdec_get_tile: unknown state_dtype");
+    if (schedule < 0 || schedule > 2) return set_error(LPDEC_EINVAL, "lpdec_get_tile: unknown schedule");
+    lpdec_params p;
+    lpdec_params_default(&p);
+    p.state_dtype = state_dtype;
+    p.schedule = schedule;
+    const lpdec::Tile t = lpdec::chosen_tile(c, &p);
+    if (group_threads) *group_threads = t.group_threads;
+    if (groups) *groups = t.groups;
     return LPDEC_OK;
 }
 

@@ -15,7 +15,7 @@ namespace lpdec {
 struct Tile {
     int groups = 1;
     int group_threads = 32;
-    bool valid = false;  // set when chosen by the autotuner
+    bool valid = false;  // set when chosen by the autotuner or by hand
 };
 
 struct SliceLayout {

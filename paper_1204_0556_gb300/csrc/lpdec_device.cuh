@@ -750,8 +750,9 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
                 const float x = __saturatef((acc - gi * p.mu_inv) * inv_dv);
                 sm.x[i] = x;
                 if (fold) {
+                    const float rx = p.rho * x;
 #pragma unroll
-                    for (int s = 0; s < DV; ++s) sm.w[es[s]] = st<S>(fmaf(p.rho, x, p.omr * wv[s]));
+                    for (int s = 0; s < DV; ++s) sm.w[es[s]] = st<S>(fmaf(p.omr, wv[s], rx));
                 }
             } else {
                 const int s0 = __ldg(c.col_ptr + i), s1 = __ldg(c.col_ptr + i + 1);
@@ -850,6 +851,28 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
     return true;
 }
 
+// Where frame f's inputs, outputs and parked state live.
+template <typename S>
+__device__ __forceinline__ FrameIO frame_io(const DecodeArgs &a, int f) {
+    FrameIO io;
+    const size_t off = (size_t)f * a.code.n;
+    io.llr = a.llr + off;
+    io.x = a.x_out + off;
+    io.bits = a.bits_out ? a.bits_out + off : nullptr;
+    io.iters = a.iters_out ? a.iters_out + f : nullptr;
+    io.cert = a.cert_out ? a.cert_out + f : nullptr;
+    if (a.k_state) {
+        const size_t sb = (size_t)a.code.Ep * sizeof(S);
+        io.w_state = reinterpret_cast<char *>(a.w_state) + (size_t)f * sb;
+        io.l_state = reinterpret_cast<char *>(a.l_state) + (size_t)f * sb;
+        io.k_state = a.k_state + f;
+    } else {
+        io.w_state = io.l_state = nullptr;
+        io.k_state = nullptr;
+    }
+    return io;
+}
+
 // Persistent decode kernel: each group pulls frame ids from a global counter
 // until the batch is exhausted.  DV > 0 selects the regular-code form (check
 // degree D, variable degree DV); L is the number of lanes per check.  MAXT:
@@ -899,22 +922,7 @@ __global__ void __launch_bounds__(MAXT, 1) decode_kernel(const DecodeArgs a) {
         par ^= 1;
         if (q >= a.n_frames) break;
         const int f = a.frame_list ? a.frame_list[q] : q;
-        FrameIO io;
-        const size_t off = (size_t)f * a.code.n;
-        io.llr = a.llr + off;
-        io.x = a.x_out + off;
-        io.bits = a.bits_out ? a.bits_out + off : nullptr;
-        io.iters = a.iters_out ? a.iters_out + f : nullptr;
-        io.cert = a.cert_out ? a.cert_out + f : nullptr;
-        if (a.k_state) {
-            const size_t sb = (size_t)a.code.Ep * sizeof(S);
-            io.w_state = reinterpret_cast<char *>(a.w_state) + (size_t)f * sb;
-            io.l_state = reinterpret_cast<char *>(a.l_state) + (size_t)f * sb;
-            io.k_state = a.k_state + f;
-        } else {
-            io.w_state = io.l_state = nullptr;
-            io.k_state = nullptr;
-        }
+        const FrameIO io = frame_io<S>(a, f);
         if (!frame_run<D, L, DV, S>(cv, a.cfg, a.iters_this_launch, io, sm, t, T, bar, phase)) break;
     }
     if (t == 0) bulk_wait_all();
@@ -952,7 +960,11 @@ constexpr int kMixedMaxThreads = LPDEC_MIXED_MAX_THREADS;
 
 // Kernel forms a code can run in (check degree class D, lanes per check L,
 // regular variable degree DV or 0).
-enum MixedKind : int { kK6R3 = 0, kK6 = 1, kK8R4 = 2, kK8 = 3, kK16 = 4, kK20 = 5, kK32 = 6, kNumKinds = 7 };
+enum MixedKind : int {
+    kK6R3 = 0, kK6 = 1, kK8R4 = 2, kK8 = 3, kK16 = 4, kK20 = 5, kK32 = 6,
+    kK16R3 = 7, kK20R3 = 8, kK32R3 = 9,  // regular codes with degree-3 variables in the wide classes
+    kNumKinds = 10
+};
 
 struct MixedCode {
     CodeView view;

@@ -48,10 +48,8 @@ int form_of(int reg_dv, bool stage) {
 }
 
 const void *decode_fn_for(int dtype, int form) {
-    if constexpr (kRegDV > 0) {
-        if (form == 2) return decode_fn_dtype<kRegDV, true>(dtype);
-        if (form == 1) return decode_fn_dtype<kRegDV, false>(dtype);
-    }
+    if (form == 2) return decode_fn_dtype<kRegDV, true>(dtype);
+    if (form == 1) return decode_fn_dtype<kRegDV, false>(dtype);
     return decode_fn_dtype<0, false>(dtype);
 }
 
@@ -101,11 +99,9 @@ cudaError_t LPDEC_CAT(occupancy_decode_, LPDEC_D)(int dtype, int reg_dv, bool st
 
 cudaError_t LPDEC_CAT(launch_decode_, LPDEC_D)(int dtype, int reg_dv, const DecodeArgs &a, const LaunchCfg &lc) {
     if (lc.block > kMaxT) return cudaErrorInvalidConfiguration;
-    if constexpr (kRegDV > 0) {
-        const int form = form_of(reg_dv, a.slice_base > 0);
-        if (form == 2) return launch_dv<kRegDV, true>(dtype, a, lc);
-        if (form == 1) return launch_dv<kRegDV, false>(dtype, a, lc);
-    }
+    const int form = form_of(reg_dv, a.slice_base > 0);
+    if (form == 2) return launch_dv<kRegDV, true>(dtype, a, lc);
+    if (form == 1) return launch_dv<kRegDV, false>(dtype, a, lc);
     return launch_dv<0, false>(dtype, a, lc);
 }
 

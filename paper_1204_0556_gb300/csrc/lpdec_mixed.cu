@@ -91,6 +91,9 @@ __global__ void __launch_bounds__(kMixedMaxThreads, 1) mixed_kernel(const MixedA
                 case kK8: mixed_round<8, 1, 0, S>(&cur_code, b, smem_raw, g, t); break;
                 case kK16: mixed_round<16, 2, 0, S>(&cur_code, b, smem_raw, g, t); break;
                 case kK20: mixed_round<20, 4, 0, S>(&cur_code, b, smem_raw, g, t); break;
+                case kK16R3: mixed_round<16, 2, 3, S>(&cur_code, b, smem_raw, g, t); break;
+                case kK20R3: mixed_round<20, 4, 3, S>(&cur_code, b, smem_raw, g, t); break;
+                case kK32R3: mixed_round<32, 4, 3, S>(&cur_code, b, smem_raw, g, t); break;
                 default: mixed_round<32, 4, 0, S>(&cur_code, b, smem_raw, g, t); break;
             }
         }
@@ -126,9 +129,9 @@ int kind_of(const lpdec_code *c) {
     switch (kClassD[c->cls]) {
         case 6: return c->reg_dv == 3 ? kK6R3 : kK6;
         case 8: return c->reg_dv == 4 ? kK8R4 : kK8;
-        case 16: return kK16;
-        case 20: return kK20;
-        default: return kK32;
+        case 16: return c->reg_dv == 3 ? kK16R3 : kK16;
+        case 20: return c->reg_dv == 3 ? kK20R3 : kK20;
+        default: return c->reg_dv == 3 ? kK32R3 : kK32;
     }
 }
 

@@ -41,7 +41,7 @@ EXPORTED = [
     "lpdec_server_create", "lpdec_server_add_code", "lpdec_server_submit", "lpdec_server_poll",
     "lpdec_server_stats", "lpdec_server_destroy", "lpdec_autotune", "lpdec_set_tile", "lpdec_server_counters",
     "lpdec_mixed_plan_create", "lpdec_mixed_plan_decode", "lpdec_mixed_plan_destroy",
-    "lpdec_decode_dual", "lpdec_dual_set_tile",
+    "lpdec_decode_dual", "lpdec_dual_set_tile", "lpdec_set_streamed_tile", "lpdec_get_tile",
 ]
 
 
@@ -116,6 +116,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
             "lpdec_mixed_plan_destroy": (ctypes.c_int, [_vp]),
             "lpdec_decode_dual": (ctypes.c_int, [_vp, _i32, _vp, ctypes.c_double, _i32, _vp, _vp, _vp, _vp, _vp]),
             "lpdec_dual_set_tile": (ctypes.c_int, [_vp, _i32, _i32]),
+            "lpdec_set_streamed_tile": (ctypes.c_int, [_vp, _i32, _i32, _i32]),
+            "lpdec_get_tile": (ctypes.c_int, [_vp, _i32, _i32, _i32p, _i32p]),
         })
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -250,6 +252,16 @@ def lpdec_autotune(handle: int, params, n_frames: int, llr_ptr: int, stream_ptr:
 
 def lpdec_set_tile(handle: int, state_dtype: int, group_threads: int, groups: int) -> None:
     _check(load().lpdec_set_tile(handle, state_dtype, group_threads, groups))
+
+
+def lpdec_set_streamed_tile(handle: int, state_dtype: int, group_threads: int, groups: int) -> None:
+    _check(load().lpdec_set_streamed_tile(handle, state_dtype, group_threads, groups))
+
+
+def lpdec_get_tile(handle: int, state_dtype: int, schedule: int) -> dict:
+    gt, g = _i32(), _i32()
+    _check(load().lpdec_get_tile(handle, state_dtype, schedule, ctypes.byref(gt), ctypes.byref(g)))
+    return {"group_threads": gt.value, "groups": g.value}
 
 
 def lpdec_mixed_plan_create(handles, frame_code, params) -> int:

@@ -189,6 +189,36 @@ def test_wide_regular_streamed_equals_resident(gpu, name, eps, iters):
         assert np.array_equal(a[k], b[k]), k
 
 
+@pytest.mark.parametrize("name,state,eps", [("C1056", "f32", 0.0), ("C1056", "f32", 1e-5), ("C1056", "bf16", 1e-5),
+                                            ("C4000", "f32", 0.0), ("C8000", "f16", 1e-5)])
+def test_streamed_tile_equals_resident(gpu, name, state, eps):
+    """A STREAMED tile set apart from the RESIDENT one (same group width, more
+    frames per CTA) gives the RESIDENT outputs, for any iterations per launch."""
+    import torch
+
+    code = _shape(name)
+    llr = I.awgn_llr(code, 2.5, 40 if name == "C1056" else 12, 606)
+    dt = {"f32": 0, "bf16": 1, "f16": 2}[state]
+    d_llr = torch.from_numpy(llr).cuda()
+    C = gpu.Code(code)
+    try:
+        # the same group width on both schedules: the stopping test's partial sums follow it
+        T = {"C1056": 64, "C4000": 256, "C8000": 512}[name]
+        gpu.lpdec_set_tile(C.handle, dt, T, 1)
+        pr = gpu.make_params(eps=eps, max_iter=60, state=state, schedule="resident")
+        a = {k: v.cpu().numpy() for k, v in gpu.decode(C, d_llr, pr).items()}
+        gpu.lpdec_set_streamed_tile(C.handle, dt, T, 2 if name != "C8000" else 1)
+        assert gpu.lpdec_get_tile(C.handle, dt, gpu.SCHED_RESIDENT) == {"group_threads": T, "groups": 1}
+        assert gpu.lpdec_get_tile(C.handle, dt, gpu.SCHED_STREAMED)["group_threads"] == T
+        for ipl in (1, 4):
+            ps = gpu.make_params(eps=eps, max_iter=60, state=state, schedule="streamed", iters_per_launch=ipl)
+            b = {k: v.cpu().numpy() for k, v in gpu.decode(C, d_llr, ps).items()}
+            for k in a:
+                assert np.array_equal(a[k], b[k]), (ipl, k)
+    finally:
+        C.close()
+
+
 def test_streamed_autotune_keeps_results(gpu, c1056):
     """Tuning the STREAMED tile changes neither the results nor the RESIDENT tile."""
     import torch
