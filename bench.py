@@ -156,9 +156,9 @@ def algorithmic_ops_per_frame_iter(code) -> int:
 KERNEL_SOURCES = ("lpdec_device.cuh", "lpdec_kclass.cuh", "lpdec_internal.h")
 MEASURED_TRAFFIC = {
     # "code/schedule": (source hash, bytes per frame per launch, capture)
-    "C1056/resident": ("3ccf32cee5bce70f", (33_859_584 + 2_085_888) / 8000,
+    "C1056/resident": ("3e8e52e66c3ae348", (33_870_848 + 1_852_672) / 8000,
                  "profiles/decode_kernel_resident_C1056_small.md: 8000 frames x 300 iterations in one launch (tile 128 x 2)"),
-    "C1056/streamed": ("3ccf32cee5bce70f", (236_629_248 + 141_584_384) / 8000,
+    "C1056/streamed": ("3e8e52e66c3ae348", (236_646_144 + 141_754_368) / 8000,
                  "profiles/decode_kernel_streamed_C1056_small.md: one iteration of 8000 frames per launch (tile 128 x 2)"),
 }
 
@@ -833,7 +833,7 @@ def main():
         "config": {"workload": f"{code.name}: n={code.n} m={code.m} seed {CODE_SEEDS[code.name]}"
                                f"{', 4-cycle free' if code.name in ('C1056', 'C2640') else ''}; {F} frames "
                                f"({per} at each of 1.5/2.0/2.5/3.0 dB), mu=3 rho=1.9, {ITERS} fixed iterations, "
-                               f"FP32 arithmetic, {args.state} z/lambda state",
+                               f"FP32 arithmetic, {args.state} edge state (w = z - lambda/mu, lambda/mu)",
                    "schedule": args.schedule, "frames_per_step": F * ws, "tile": tile,
                    "l2": f"inputs larger than L2: {F * code.n * 4 / 1e6:.0f} MB of LLRs read and "
                          f"{F * code.n * 4 / 1e6:.0f} MB of x written per step",

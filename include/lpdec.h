@@ -52,7 +52,9 @@ extern "C" {
  * that frame is not decoded (x = 0, bits = 0, cert = 0). */
 #define LPDEC_FRAME_BAD_LLR (-1)
 
-/* ---- storage type of the per-edge z / lambda state --------------------- */
+/* ---- storage type of the per-edge state --------------------------------- */
+/* (The kernels keep w = z - lambda/mu and lambda/mu per edge; Algorithm 1's z
+ * is w + lambda/mu.) */
 #define LPDEC_STATE_F32  0
 #define LPDEC_STATE_BF16 1 /* round-to-nearest-even on every store; FP32 arithmetic */
 #define LPDEC_STATE_F16  2 /* round-to-nearest-even on every store; FP32 arithmetic */
@@ -60,7 +62,7 @@ extern "C" {
 /* ---- schedules --------------------------------------------------------- */
 #define LPDEC_SCHED_AUTO     0 /* RESIDENT when a frame's state fits in shared memory, else STREAMED */
 #define LPDEC_SCHED_STREAMED 1 /* one kernel launch per ADMM iteration (or iters_per_launch); the
-                                  z/lambda state of every frame goes through device memory between
+                                  edge state of every frame goes through device memory between
                                   launches */
 #define LPDEC_SCHED_RESIDENT 2 /* one launch; each frame's z/lambda/x state stays in shared memory
                                   for all of its iterations */

@@ -99,7 +99,7 @@ struct Pool {
     float *llr = nullptr, *x = nullptr, *d_new_llr = nullptr, *d_xo = nullptr;
     uint8_t *bits = nullptr, *cert = nullptr, *d_bo = nullptr, *d_co = nullptr;
     int32_t *iters = nullptr, *kst = nullptr, *d_kc = nullptr, *d_io = nullptr;
-    void *zst = nullptr, *lst = nullptr;
+    void *wst = nullptr, *lst = nullptr;  // parked w = z - lambda/mu and lambda/mu, [slots x Ep]
     int *d_active = nullptr, *d_new_slots = nullptr, *d_fin = nullptr, *d_queue = nullptr;
     float *h_new_llr = nullptr, *h_xo = nullptr;
     int *h_new_slots = nullptr, *h_active = nullptr, *h_fin = nullptr;
@@ -158,7 +158,7 @@ int pool_alloc(lpdec_server *sv, Pool &P, int slots) {
     size_t off = 0;
     auto take = [&](size_t b) { size_t o = off; off += align256(b); return o; };
     const size_t o_llr = take((size_t)slots * n * 4), o_x = take((size_t)slots * n * 4), o_bits = take((size_t)slots * n),
-                 o_iters = take((size_t)slots * 4), o_cert = take((size_t)slots), o_z = take((size_t)slots * sb),
+                 o_iters = take((size_t)slots * 4), o_cert = take((size_t)slots), o_w = take((size_t)slots * sb),
                  o_l = take((size_t)slots * sb), o_k = take((size_t)slots * 4), o_act = take((size_t)slots * 4),
                  o_ns = take((size_t)slots * 4), o_nl = take((size_t)slots * n * 4), o_kc = take((size_t)slots * 4),
                  o_fin = take((size_t)slots * 4), o_xo = take((size_t)slots * n * 4), o_bo = take((size_t)slots * n),
@@ -172,7 +172,7 @@ int pool_alloc(lpdec_server *sv, Pool &P, int slots) {
     P.bits = reinterpret_cast<uint8_t *>(d + o_bits);
     P.iters = reinterpret_cast<int32_t *>(d + o_iters);
     P.cert = reinterpret_cast<uint8_t *>(d + o_cert);
-    P.zst = d + o_z;
+    P.wst = d + o_w;
     P.lst = d + o_l;
     P.kst = reinterpret_cast<int32_t *>(d + o_k);
     P.d_active = reinterpret_cast<int *>(d + o_act);
@@ -291,7 +291,7 @@ int run_round(lpdec_server *sv) {
         a.bits_out = P.bits;
         a.iters_out = P.iters;
         a.cert_out = P.cert;
-        a.w_state = P.zst;
+        a.w_state = P.wst;
         a.l_state = P.lst;
         a.k_state = P.kst;
         a.iters_this_launch = P.params.iters_per_launch;
