@@ -145,19 +145,25 @@ extern "C" int lpdec_code_create(int32_t n, int32_t m, const int32_t *row_ptr, c
     c->k_rank = gf2_k_rank(n, m, row_ptr, col_idx);
     c->cls = lpdec::degree_class(max_dc);
     // Regular codes (one check degree, one variable degree) run the regular-code
-    // kernel, which takes edge offsets from j*dc and i*dv: (3,6)-type codes in
-    // the class D = 6, (4,8) in D = 8 (check degree equal to the class width),
-    // and degree-3 variables with any check degree in the wide classes.
+    // kernel, which takes variable edges from i*dv slots and check edges from
+    // j*dc: (3,6)-type codes in the class D = 6 and (4,8) in D = 8 (check degree
+    // equal to the class width); in the wide classes, any code whose variables
+    // all have degree 3 (reg_dc = 0 when the check degrees differ: the check
+    // update then takes its edge range from row_ptr).
     {
         const int dc0 = row_ptr[1] - row_ptr[0], dv0 = col_ptr[1] - col_ptr[0];
-        bool reg = true;
-        for (int j = 0; j < m && reg; ++j) reg = (row_ptr[j + 1] - row_ptr[j]) == dc0;
-        for (int i = 0; i < n && reg; ++i) reg = (col_ptr[i + 1] - col_ptr[i]) == dv0;
+        bool reg_c = true, reg_v = true;
+        for (int j = 0; j < m && reg_c; ++j) reg_c = (row_ptr[j + 1] - row_ptr[j]) == dc0;
+        for (int i = 0; i < n && reg_v; ++i) reg_v = (col_ptr[i + 1] - col_ptr[i]) == dv0;
         const int D = lpdec::kClassD[c->cls];
-        const int want_dv = D == 8 ? 4 : 3;
-        reg = reg && dv0 == want_dv && (D > 8 || dc0 == D);
-        c->reg_dv = reg ? dv0 : 0;
-        c->reg_dc = reg ? dc0 : 0;
+        if (D <= 8) {
+            const bool reg = reg_c && reg_v && dv0 == (D == 8 ? 4 : 3) && dc0 == D;
+            c->reg_dv = reg ? dv0 : 0;
+            c->reg_dc = reg ? dc0 : 0;
+        } else {
+            c->reg_dv = (reg_v && dv0 == 3) ? 3 : 0;
+            c->reg_dc = (c->reg_dv && reg_c) ? dc0 : 0;
+        }
     }
     cudaError_t err = cudaGetDevice(&c->device);
     if (err != cudaSuccess) { delete c; return cuda_error(err, "lpdec_code_create: cudaGetDevice"); }

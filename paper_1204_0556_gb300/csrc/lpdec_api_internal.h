@@ -50,7 +50,7 @@ struct lpdec_code {
     int n = 0, m = 0, E = 0, Ep = 0;
     int max_dc = 0, k_rank = 0, cls = 0, device = 0;
     int reg_dv = 0;             // variable degree if the code runs the regular-code kernel, else 0
-    int reg_dc = 0;             // the common check degree of such a code
+    int reg_dc = 0;             // its common check degree, or 0 when check degrees differ (wide classes)
     void *dev_block = nullptr;  // one allocation holding the four index arrays
     int32_t *row_ptr = nullptr, *col_idx = nullptr, *col_ptr = nullptr, *csc_edge = nullptr;
     // Regular codes: 16-bit index block (CodeView::col16 / csc16), else null.

@@ -237,7 +237,8 @@ struct CodeView {
     const uint16_t *csc16;
     int idx16_bytes;
     int col16_elems;
-    int reg_dc;               // regular codes: the common check degree (check j owns edges j*reg_dc ...)
+    int reg_dc;               // regular-code kernels: the common check degree (check j owns edges
+                              // j*reg_dc ...), or 0 when check degrees differ (wide classes only)
 };
 
 struct IterCfg {
@@ -434,9 +435,10 @@ __device__ __forceinline__ int seg_min_i(int x) {
 // need_res, the residual terms re-read the old w and lambda/mu before they are
 // overwritten.  (One instantiation with a runtime flag: two inlined copies of
 // this update exceed the 64-register budget of the 1024-thread kernel.)
-// DV > 0: regular code (every check has degree c.reg_dc, every variable DV):
-// edge offsets j*reg_dc, 16-bit column indices, and in iterations without
-// residuals with FP32 state ws holds u = rho x + (1 - rho) w (see frame_run).
+// DV > 0: every variable has degree DV: 16-bit column indices, and in
+// iterations without residuals with FP32 state ws holds u = rho x + (1 - rho) w
+// (see frame_run).  Check j's edges start at j*reg_dc when every check has
+// degree reg_dc, else at row_ptr[j].
 template <int D, int L, int DV, typename S>
 __device__ __forceinline__ void check_update_seg(const CodeView &c, const IterCfg &p, int j, bool valid,
                                                  S *ws, S *ls, const float *xs, bool need_res,
@@ -446,7 +448,7 @@ __device__ __forceinline__ void check_update_seg(const CodeView &c, const IterCf
     const int r = threadIdx.x & (L - 1);
     int e0 = 0, d = 0;
     if (valid) {
-        if constexpr (DV > 0) {
+        if (DV > 0 && c.reg_dc > 0) {
             d = c.reg_dc;
             e0 = j * d;
         } else {
