@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--variants", type=int, default=1, help="also time the other schedules/precisions")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-latency", action="store_true", help="skip the served p50/p99 leg of the headline")
+    ap.add_argument("--latency-rate", type=float, default=5e4, help="offered frames/s of the headline's served leg")
     ap.add_argument("--workload", default="single",
                     choices=["single", "mixed", "precision", "served", "bsc", "sweep", "dual"],
                     help="single: the headline C1056 batch; mixed: three codes in one persistent launch; "
@@ -563,6 +565,57 @@ def run_served(args):
     print(json.dumps(line), flush=True)
 
 
+def served_latency(lpdec, C, code, llr_h, rate: float, seconds: float, round_iters: int) -> dict:
+    """The headline's frames and parameters (300 fixed iterations, FP32) served as
+    a Poisson stream of one-frame requests through lpdec_server: p50/p99 latency
+    from submit to completion, and the sustained bits/s."""
+    import ctypes
+
+    R = max(1, int(rate * seconds))
+    arrivals = np.cumsum(np.random.Generator(np.random.Philox(key=9)).exponential(1.0 / rate, R))
+    p = lpdec.make_params(mu=MU, rho=RHO, eps=0.0, max_iter=ITERS, state="f32", iters_per_launch=round_iters)
+    srv = lpdec.Server(budget_bytes=8 << 30)
+    cid = srv.add_code(C)
+    F = len(llr_h)
+    idx = np.arange(R) * max(1, F // R) % F  # frames spread over the four Eb/N0 points
+    ptrs = [llr_h[i].ctypes.data for i in idx]
+    sub_fn = lpdec.load().lpdec_server_submit
+    poll_fn = lpdec.load().lpdec_server_poll
+    rid = np.zeros(R, dtype=np.uint64)
+    rid_c = ctypes.c_uint64()
+    submitted = [0]
+    outx = np.empty(code.n, np.float32)
+
+    def poller():
+        for i in range(R):
+            while submitted[0] <= i:
+                time.sleep(0.0002)
+            if poll_fn(srv.handle, int(rid[i]), -1, outx.ctypes.data, None, None, None) != 0:
+                raise RuntimeError(lpdec.lpdec_last_error())
+
+    th = threading.Thread(target=poller)
+    th.start()
+    t0 = time.perf_counter()
+    for i in range(R):
+        while time.perf_counter() - t0 < arrivals[i]:
+            pass
+        st = sub_fn(srv.handle, cid, 1, ptrs[i], ctypes.byref(p), ctypes.byref(rid_c))
+        while st == lpdec.LPDEC_EBUSY:
+            time.sleep(0.0005)
+            st = sub_fn(srv.handle, cid, 1, ptrs[i], ctypes.byref(p), ctypes.byref(rid_c))
+        if st != 0:
+            raise RuntimeError(lpdec.lpdec_last_error())
+        rid[i] = rid_c.value
+        submitted[0] = i + 1
+    th.join()
+    stats = srv.stats()
+    srv.close()
+    return {"p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"], "sustained_bits_per_s": stats["bits_per_s"],
+            "offered_frames_per_s": rate, "frames": int(stats["frames"]), "iters_per_round": round_iters,
+            "note": f"the headline's C1056 frames and parameters ({ITERS} fixed iterations, FP32) as Poisson "
+                    "one-frame requests through lpdec_server; latency from submit to completion"}
+
+
 def run_bsc(args):
     """Random (3,6) n=1002 ensemble over the BSC: WER, BER, iterations split by outcome, ML lower bound."""
     import torch
@@ -861,6 +914,9 @@ def main():
                                   "hbm_frac": round(vach / hbm_peak, 4), "launches_per_step": vl,
                                   "tile": vtile}
         line["variants"] = var
+
+    if not args.no_latency and ws == 1:
+        line["latency"] = served_latency(lpdec, C, code, llr_h, rate=args.latency_rate, seconds=1.0, round_iters=8)
 
     if not args.no_e2e:
         # end to end through the host entry point: pinned LLRs in, bits/iters/cert out, every step

@@ -87,6 +87,42 @@ static int gf2_k_rank(int n, int m, const int32_t *row_ptr, const int32_t *col_i
     return n - rank;
 }
 
+// Order each variable's edges within its index slots so that the 32 variables
+// a warp handles together touch as few shared-memory banks twice as possible in
+// every slot: the x-update gathers w (and, folding, scatters u) slot by slot, and
+// w[e] of FP32 state sits in bank e mod 32.  Greedy over the permutations of each
+// variable's edges, three passes per block of 32 variables.  Only the order of a
+// variable's (commutative) sum changes.
+static void order_edge_slots(uint16_t *csc, int n, int dv) {
+    for (int b0 = 0; b0 < n; b0 += 32) {
+        const int b1 = std::min(n, b0 + 32);
+        int cnt[4][32] = {};
+        for (int i = b0; i < b1; ++i)
+            for (int s = 0; s < dv; ++s) ++cnt[s][csc[(size_t)i * 4 + s] & 31];
+        for (int pass = 0; pass < 3; ++pass) {
+            for (int i = b0; i < b1; ++i) {
+                uint16_t *v = csc + (size_t)i * 4;
+                for (int s = 0; s < dv; ++s) --cnt[s][v[s] & 31];
+                uint16_t cur[4] = {v[0], v[1], v[2], v[3]};
+                uint16_t best[4] = {v[0], v[1], v[2], v[3]};
+                int best_cost = 0;
+                for (int s = 0; s < dv; ++s) best_cost += cnt[s][cur[s] & 31];
+                std::sort(cur, cur + dv);
+                do {
+                    int cost = 0;
+                    for (int s = 0; s < dv; ++s) cost += cnt[s][cur[s] & 31];
+                    if (cost < best_cost) {
+                        best_cost = cost;
+                        std::copy(cur, cur + dv, best);
+                    }
+                } while (std::next_permutation(cur, cur + dv));
+                std::copy(best, best + dv, v);
+                for (int s = 0; s < dv; ++s) ++cnt[s][v[s] & 31];
+            }
+        }
+    }
+}
+
 extern "C" int lpdec_code_create(int32_t n, int32_t m, const int32_t *row_ptr, const int32_t *col_idx,
                                  const int32_t *col_ptr, const int32_t *row_idx, const int32_t *edge_perm,
                                  lpdec_code **out) {
@@ -200,6 +236,7 @@ extern "C" int lpdec_code_create(int32_t n, int32_t m, const int32_t *row_ptr, c
         uint16_t *csc = h16.data() + c->col16_elems;
         for (int i = 0; i < n; ++i)
             for (int s = col_ptr[i]; s < col_ptr[i + 1]; ++s) csc[(size_t)i * 4 + (s - col_ptr[i])] = (uint16_t)edge_perm[s];
+        order_edge_slots(csc, n, c->reg_dv);
         err = cudaMalloc(&c->dev_idx16, (size_t)c->idx16_bytes);
         if (err == cudaSuccess)
             err = cudaMemcpy(c->dev_idx16, h16.data(), (size_t)c->idx16_bytes, cudaMemcpyHostToDevice);
