@@ -978,6 +978,8 @@ struct MixedCode {
     int off_x, off_red;  // slice layout
     int n_frames;        // frames of this code in the batch
     const int *frames;   // [n_frames] their frame ids
+    int idx_off;         // regular codes: shared-memory offset where a CTA working on this code
+                         // stages its 16-bit index block (after the slices), or -1
 };
 
 struct MixedArgs {

@@ -79,6 +79,18 @@ __global__ void __launch_bounds__(kMixedMaxThreads, 1) mixed_kernel(const MixedA
     for (;;) {
         if (threadIdx.x == 0) cur_code = a.code[cur];
         __syncthreads();
+        if (cur_code.idx_off >= 0) {
+            // stage this code's 16-bit indices after its slices, then point the
+            // view at the copy (every thread has read the global pointer first)
+            copy16(smem_raw + cur_code.idx_off, cur_code.view.col16, cur_code.view.idx16_bytes, threadIdx.x,
+                   blockDim.x);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                cur_code.view.col16 = reinterpret_cast<const uint16_t *>(smem_raw + cur_code.idx_off);
+                cur_code.view.csc16 = cur_code.view.col16 + cur_code.view.col16_elems;
+            }
+            __syncthreads();
+        }
         const int T = cur_code.group_threads;
         const int g = threadIdx.x / T;
         if (g < cur_code.groups) {
@@ -229,6 +241,19 @@ int mixed_setup(const char *who, const lpdec_code *const *codes, int32_t n_codes
         const int g = std::min({15, kMixedMaxThreads / mc.group_threads, (int)(smem / layouts[c].bytes)});
         mc.groups = std::max(1, g);
         block = std::max(block, mc.groups * mc.group_threads);
+    }
+    // Regular codes stage their 16-bit index block after their slices when it
+    // fits in the device's shared memory (the CTA's footprint may grow to it).
+    for (int c = 0; c < n_codes; ++c) {
+        MixedCode &mc = a.code[c];
+        mc.idx_off = -1;
+        if (codes[c]->reg_dv > 0 && codes[c]->idx16_bytes > 0) {
+            const size_t off = ((size_t)mc.groups * layouts[c].bytes + 127) & ~(size_t)127;
+            if (off + (size_t)codes[c]->idx16_bytes <= (size_t)cap) {
+                mc.idx_off = (int)off;
+                smem = std::max(smem, off + (size_t)codes[c]->idx16_bytes);
+            }
+        }
     }
     S.fn = mixed_fn(p->state_dtype);
     cudaError_t err = cudaFuncSetAttribute(S.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
