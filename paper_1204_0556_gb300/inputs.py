@@ -213,6 +213,32 @@ def irregular_check_degrees(m: int, total: int, lo: int, hi: int, seed: int) -> 
     return deg.astype(np.int64)
 
 
+def random_code(n: int, m: int, dc_lo: int, dc_hi: int, seed: int, name: str = "") -> Code:
+    """Seeded code with check degrees drawn in [dc_lo, dc_hi] and irregular
+    variable degrees: a shuffled deal places every variable in one check, then
+    each check is filled with distinct random variables."""
+    rng = _rng(seed)
+    deg = rng.integers(dc_lo, dc_hi + 1, size=m)
+    if deg.sum() < n:
+        raise ValueError("too few edges to cover every variable")
+    rows = [[] for _ in range(m)]
+    order = rng.permutation(n)
+    j = 0
+    for v in order:  # round-robin over checks that still have room
+        while len(rows[j]) >= deg[j]:
+            j = (j + 1) % m
+        rows[j].append(int(v))
+        j = (j + 1) % m
+    for j in range(m):
+        have = set(rows[j])
+        while len(rows[j]) < deg[j]:
+            v = int(rng.integers(0, n))
+            if v not in have:
+                have.add(v)
+                rows[j].append(v)
+    return code_from_rows(n, [sorted(r) for r in rows], name=name)
+
+
 def socket_code(n: int, dv: int, check_degrees: Sequence[int], seed: int,
                 remove_4cycles: bool = False, max_swaps: int = 500000, name: str = "") -> Code:
     """Configuration-model code: variable sockets (dv each) matched to check sockets.

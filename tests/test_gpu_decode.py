@@ -161,11 +161,15 @@ def test_streamed_equals_resident(gpu, c1056, state):
 def _shape(name):
     if name == "S12":  # (3,12)-regular socket code: the 16-wide segmented check class
         return I.socket_code(960, 3, [12] * 240, 4, name="S12")
+    if name == "S16V4":  # (4,16): wide checks, variables not of degree 3 -> generic wide form
+        return I.socket_code(1024, 4, [16] * 256, 9, name="S16V4")
+    if name == "R20":  # checks of degree 10..20, variable degrees 1..4 -> generic wide form
+        return I.random_code(600, 60, 10, 20, 8, name="R20")
     return I.benchmark_code(name, 0)
 
 
 @pytest.mark.parametrize("name,frames,iters", [("C2640", 8, 100), ("C4000", 8, 100), ("C8000", 6, 80),
-                                               ("S12", 12, 100)])
+                                               ("S12", 12, 100), ("S16V4", 12, 100), ("R20", 16, 100)])
 def test_other_code_shapes(gpu, oracle_mod, name, frames, iters):
     code = _shape(name)
     llr = I.awgn_llr(code, 3.0, frames, 303)
@@ -175,12 +179,14 @@ def test_other_code_shapes(gpu, oracle_mod, name, frames, iters):
     assert_parity(code, got, ref, 1e-4)
 
 
-@pytest.mark.parametrize("name", ["C4000", "S12"])
+@pytest.mark.parametrize("name", ["C4000", "S12", "C8000", "S16V4", "R20"])
 @pytest.mark.parametrize("eps,iters", [(0.0, 40), (1e-5, 120)])
-def test_wide_regular_streamed_equals_resident(gpu, name, eps, iters):
-    """Regular codes with wide checks ((3,30) and (3,12)) run the regular-code
-    kernel of the segmented classes; both schedules give identical outputs, in
-    fixed-iteration runs (x folded into the edge state) and early-exit runs."""
+def test_wide_streamed_equals_resident(gpu, name, eps, iters):
+    """Wide-check codes: the regular-code kernel of the segmented classes
+    ((3,30), (3,12), and C8000's degree-3 variables with mixed check degrees)
+    and the generic form ((4,16), irregular variables).  Both schedules give
+    identical outputs, in fixed-iteration runs (x folded into the edge state in
+    the regular forms) and early-exit runs."""
     code = _shape(name)
     llr = I.awgn_llr(code, 3.0, 10, 404)
     a = gpu_decode(gpu, code, llr, eps=eps, max_iter=iters, schedule="resident")

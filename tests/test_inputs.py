@@ -82,3 +82,14 @@ def test_bsc_llr():
     mag = np.log(0.95 / 0.05)
     assert np.allclose(np.abs(g), mag, rtol=1e-6)
     assert 0.03 < (g < 0).mean() < 0.07
+
+
+def test_random_code_covers_every_variable():
+    c = I.random_code(600, 60, 10, 20, 8)
+    dc = np.diff(c.row_ptr)
+    dv = np.diff(c.col_ptr)
+    assert dc.min() >= 10 and dc.max() <= 20
+    assert dv.min() >= 1 and dv.max() > dv.min()  # irregular variable degrees, none empty
+    assert c.E == int(dc.sum()) == int(dv.sum())
+    d = I.random_code(600, 60, 10, 20, 8)
+    assert np.array_equal(c.col_idx, d.col_idx) and np.array_equal(c.edge_perm, d.edge_perm)
