@@ -213,7 +213,19 @@ __device__ __forceinline__ Proj project_pp(const float (&v)[D], int d) {
 #pragma unroll
         for (int k = 0; k < D; ++k)
             kap[k] = (k < d) ? (((th >> k) & 1u) ? v[k] - 1.0f : -v[k]) : kBigKappa;
-        pr.beta = beta_sorted<D>(kap, d);
+        // One active breakpoint: with kappa_(1) <= kappa_(2) the two smallest,
+        // beta* = 1 + kappa_(1) exactly when kappa_(2) >= 1 + kappa_(1) (then only
+        // kappa_(1) lies below beta*).  This holds for most violated checks once a
+        // frame has settled, and skips the sort; otherwise sort and scan.
+        float k1 = fminf(kap[0], D > 1 ? kap[1] : kBigKappa);
+        float k2 = D > 1 ? fmaxf(kap[0], kap[1]) : kBigKappa;
+#pragma unroll
+        for (int k = 2; k < D; ++k) {
+            k2 = fminf(k2, fmaxf(k1, kap[k]));
+            k1 = fminf(k1, kap[k]);
+        }
+        const float c1 = 1.0f + k1;
+        pr.beta = k2 >= c1 ? fmaxf(c1, 0.0f) : beta_sorted<D>(kap, d);
     } else {
         pr.beta = beta_fixed_point<D>(v, d, th);
     }
