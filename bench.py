@@ -158,9 +158,9 @@ def algorithmic_ops_per_frame_iter(code) -> int:
 KERNEL_SOURCES = ("lpdec_device.cuh", "lpdec_kclass.cuh", "lpdec_internal.h")
 MEASURED_TRAFFIC = {
     # "code/schedule": (source hash, bytes per frame per launch, capture)
-    "C1056/resident": ("3e8e52e66c3ae348", (33_870_848 + 1_852_672) / 8000,
+    "C1056/resident": ("ce2c00130157f322", (33_861_376 + 1_797_120) / 8000,
                  "profiles/decode_kernel_resident_C1056_small.md: 8000 frames x 300 iterations in one launch (tile 128 x 2)"),
-    "C1056/streamed": ("3e8e52e66c3ae348", (236_646_144 + 141_754_368) / 8000,
+    "C1056/streamed": ("ce2c00130157f322", (236_644_608 + 141_235_712) / 8000,
                  "profiles/decode_kernel_streamed_C1056_small.md: one iteration of 8000 frames per launch (tile 128 x 2)"),
 }
 
