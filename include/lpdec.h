@@ -22,6 +22,10 @@
  *     per-frame residual norms of the stopping test.
  *   - Layouts are row-major: an LLR or x batch is [n_frames x n], frame f at
  *     element offset f*n.
+ *   - Threads: decode calls on the same code from several host threads (and
+ *     streams) are safe; they only read the code object.  The calls that change
+ *     a code's tiles (lpdec_autotune, lpdec_set_tile, lpdec_set_streamed_tile,
+ *     lpdec_dual_set_tile) must not run while another thread uses that code.
  */
 #ifndef LPDEC_H
 #define LPDEC_H

@@ -659,9 +659,14 @@ extern "C" int lpdec_autotune(lpdec_code *c, const lpdec_params *p, int32_t n_fr
     if (err != cudaSuccess) return cuda_error(err, "lpdec_autotune: cudaMallocAsync");
     float *x = reinterpret_cast<float *>(buf);
     void *work = buf + ((nx * 4 + 255) & ~(size_t)255);
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    err = cudaEventCreate(&e0);
+    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    if (err != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        cudaFreeAsync(buf, stream);
+        return cuda_error(err, "lpdec_autotune: cudaEventCreate");
+    }
     double best = 1e30;
     lpdec::Tile best_t = cand[0];
     rc = LPDEC_OK;
