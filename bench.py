@@ -48,7 +48,8 @@ def parse():
                     help="code of the single-code workload (the headline is C1056)")
     ap.add_argument("--iters", type=int, default=300, help="fixed ADMM iterations of the single-code workload")
     ap.add_argument("--no-autotune", action="store_true", help="use the library's default tile")
-    ap.add_argument("--tile", default="", help="GROUP_THREADS,GROUPS: set the single-code tile instead of autotuning")
+    ap.add_argument("--tile", default="", help="GROUP_THREADS,GROUPS[,RING_SLOTS]: set the single-code tile instead of "
+                    "autotuning (RING_SLOTS > GROUPS: the STREAMED ring kernel)")
     ap.add_argument("--schedule", default="resident", choices=["resident", "streamed", "auto"])
     ap.add_argument("--state", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--variants", type=int, default=1, help="also time the other schedules/precisions")
@@ -782,9 +783,13 @@ def main():
     C = lpdec.Code(code)
     tile = None
     if args.tile:
-        gt, g = (int(v) for v in args.tile.split(","))
-        lpdec.lpdec_set_tile(C.handle, {"f32": 0, "bf16": 1, "f16": 2}[args.state], gt, g)
+        gt, g, *ring = (int(v) for v in args.tile.split(","))
+        dt = {"f32": 0, "bf16": 1, "f16": 2}[args.state]
+        lpdec.lpdec_set_tile(C.handle, dt, gt, g)
         tile = {"group_threads": gt, "groups": g, "source": "--tile"}
+        if ring and ring[0]:
+            lpdec.lpdec_set_streamed_tile(C.handle, dt, gt, g, ring[0])
+            tile["ring_slots"] = ring[0]
     tune_sample = []
 
     def tune(schedule, state):

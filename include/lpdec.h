@@ -141,7 +141,9 @@ LPDEC_API int lpdec_code_destroy(lpdec_code *code);
  * [n_frames x n]) with params, keep the fastest for that state dtype and
  * schedule in the code object, and report it.  params.schedule = STREAMED
  * tunes the STREAMED tile (with params.max_iter launches per candidate, so a
- * few iterations suffice); RESIDENT or AUTO tunes the RESIDENT tile.  Later
+ * few iterations suffice); its candidates include ring tiles (see
+ * lpdec_set_streamed_tile), reported through lpdec_get_tile.  RESIDENT or AUTO
+ * tunes the RESIDENT tile.  Later
  * decodes of the code use the tile of their schedule (STREAMED decodes fall
  * back to the RESIDENT tile when no STREAMED tile was tuned); the server and
  * lpdec_decode_mixed use the RESIDENT tile.
@@ -156,15 +158,22 @@ LPDEC_API int lpdec_autotune(lpdec_code *code, const lpdec_params *params, int32
 LPDEC_API int lpdec_set_tile(lpdec_code *code, int32_t state_dtype, int32_t group_threads, int32_t groups);
 
 /* Set a code's STREAMED tile for one state dtype by hand (the RESIDENT tile is
- * left as it is); 0, 0 restores the fallback to the RESIDENT tile.
- * LPDEC_EINVAL for a tile that does not fit. */
-LPDEC_API int lpdec_set_streamed_tile(lpdec_code *code, int32_t state_dtype, int32_t group_threads, int32_t groups);
+ * left as it is); 0, 0, 0 restores the fallback to the RESIDENT tile.
+ * ring_slots = 0: the plain STREAMED kernel, each group loading its frame's
+ * parked state into its own slice.  ring_slots = R > 0 (groups < R <= 64): a
+ * producer warp per CTA (groups x group_threads + 32 threads) prefetches the
+ * parked state of the next frames into a ring of R shared-memory slots while
+ * the groups compute; results are identical.  LPDEC_EINVAL for a tile that
+ * does not fit. */
+LPDEC_API int lpdec_set_streamed_tile(lpdec_code *code, int32_t state_dtype, int32_t group_threads, int32_t groups,
+                                      int32_t ring_slots);
 
 /* The tile a decode of this code with this state dtype and schedule
- * (LPDEC_SCHED_*) would use now: tuned, set by hand, or the default.  Any
+ * (LPDEC_SCHED_*) would use now: tuned, set by hand, or the default;
+ * ring_slots is 0 unless a STREAMED decode would run the ring kernel.  Any
  * output pointer may be NULL. */
 LPDEC_API int lpdec_get_tile(const lpdec_code *code, int32_t state_dtype, int32_t schedule, int32_t *group_threads,
-                             int32_t *groups);
+                             int32_t *groups, int32_t *ring_slots);
 
 /* ---- decoding ---------------------------------------------------------- */
 

@@ -278,22 +278,23 @@ extern "C" int lpdec_code_destroy(lpdec_code *c) {
 // launch plumbing
 namespace lpdec {
 
-static cudaError_t class_prepare(const lpdec_code *c, int dtype, bool stage, size_t smem) {
+static cudaError_t class_prepare(const lpdec_code *c, int dtype, bool stage, bool ring, size_t smem) {
     switch (kClassD[c->cls]) {
-        case 6: return prepare_decode_6(dtype, c->reg_dv, stage, smem);
-        case 8: return prepare_decode_8(dtype, c->reg_dv, stage, smem);
-        case 16: return prepare_decode_16(dtype, c->reg_dv, stage, smem);
-        case 20: return prepare_decode_20(dtype, c->reg_dv, stage, smem);
-        default: return prepare_decode_32(dtype, c->reg_dv, stage, smem);
+        case 6: return prepare_decode_6(dtype, c->reg_dv, stage, ring, smem);
+        case 8: return prepare_decode_8(dtype, c->reg_dv, stage, ring, smem);
+        case 16: return prepare_decode_16(dtype, c->reg_dv, stage, ring, smem);
+        case 20: return prepare_decode_20(dtype, c->reg_dv, stage, ring, smem);
+        default: return prepare_decode_32(dtype, c->reg_dv, stage, ring, smem);
     }
 }
-static cudaError_t class_occupancy(const lpdec_code *c, int dtype, bool stage, int block, size_t smem, int *bps) {
+static cudaError_t class_occupancy(const lpdec_code *c, int dtype, bool stage, bool ring, int block, size_t smem,
+                                   int *bps) {
     switch (kClassD[c->cls]) {
-        case 6: return occupancy_decode_6(dtype, c->reg_dv, stage, block, smem, bps);
-        case 8: return occupancy_decode_8(dtype, c->reg_dv, stage, block, smem, bps);
-        case 16: return occupancy_decode_16(dtype, c->reg_dv, stage, block, smem, bps);
-        case 20: return occupancy_decode_20(dtype, c->reg_dv, stage, block, smem, bps);
-        default: return occupancy_decode_32(dtype, c->reg_dv, stage, block, smem, bps);
+        case 6: return occupancy_decode_6(dtype, c->reg_dv, stage, ring, block, smem, bps);
+        case 8: return occupancy_decode_8(dtype, c->reg_dv, stage, ring, block, smem, bps);
+        case 16: return occupancy_decode_16(dtype, c->reg_dv, stage, ring, block, smem, bps);
+        case 20: return occupancy_decode_20(dtype, c->reg_dv, stage, ring, block, smem, bps);
+        default: return occupancy_decode_32(dtype, c->reg_dv, stage, ring, block, smem, bps);
     }
 }
 static cudaError_t class_launch(const lpdec_code *c, int dtype, const DecodeArgs &a, const LaunchCfg &lc) {
@@ -379,8 +380,87 @@ Tile chosen_tile(const lpdec_code *c, const lpdec_params *p) {
     return default_tile(c, dt);
 }
 
+// Ring kernel layout (must match decode_kernel_ring): [16-bit index block,
+// when staged] [R state slots, w then lambda/mu] [G scratch areas: x, the
+// reduction scratch and 8 ints of flags] [R slot records of 32 bytes, then two
+// ints: the consumers' sequence counter and the stop flag].
+struct RingLayout {
+    size_t slot_bytes = 0, off_slots = 0, off_scratch = 0, off_meta = 0, total = 0;
+    SliceLayout scratch;  // off_x = 0
+};
+static RingLayout ring_layout(const lpdec_code *c, int dtype, const Tile &tile, size_t base) {
+    RingLayout R;
+    R.slot_bytes = (2 * (size_t)c->Ep * dtype_size(dtype) + 127) & ~(size_t)127;
+    R.scratch.off_x = 0;
+    R.scratch.off_red = ((size_t)c->n * 4 + 15) & ~(size_t)15;
+    R.scratch.bytes = (R.scratch.off_red + (size_t)(tile.group_threads / 32) * 2 * 4 + 8 * 4 + 127) & ~(size_t)127;
+    R.off_slots = base;
+    R.off_scratch = R.off_slots + (size_t)tile.ring * R.slot_bytes;
+    R.off_meta = R.off_scratch + (size_t)tile.groups * R.scratch.bytes;
+    R.total = R.off_meta + (size_t)tile.ring * 32 + 16;
+    return R;
+}
+
+size_t ring_smem_bytes(const lpdec_code *c, int dtype, const Tile &tile, bool stage) {
+    if (tile.ring <= tile.groups || tile.ring > 64) return 0;
+    const size_t base = stage ? (((size_t)c->idx16_bytes + 127) & ~(size_t)127) : 0;
+    return ring_layout(c, dtype, tile, base).total;
+}
+
+static int plan_ring(const lpdec_code *c, int dtype, const Tile &tile, int n_frames, cudaStream_t stream,
+                     LaunchCfg *lc, SliceLayout *layout) {
+    const int block = tile.groups * tile.group_threads + 32;  // + the producer warp
+    if (block > class_max_threads(c->cls) || tile.groups < 1 || tile.groups > 15 || tile.group_threads % 32 ||
+        tile.group_threads < 32 || tile.ring <= tile.groups || tile.ring > 64)
+        return set_error(LPDEC_EINVAL, "invalid ring tile: %d groups x %d threads, %d slots", tile.groups,
+                         tile.group_threads, tile.ring);
+    const size_t cap = (size_t)device_smem_optin(c->device);
+    bool stage = c->reg_dv > 0 && c->idx16_bytes > 0 && ring_smem_bytes(c, dtype, tile, true) <= cap;
+    const size_t base = stage ? (((size_t)c->idx16_bytes + 127) & ~(size_t)127) : 0;
+    const RingLayout R = ring_layout(c, dtype, tile, base);
+    if (R.total > cap)
+        return set_error(LPDEC_EINVAL, "ring of %d slots of %zu bytes and %d groups does not fit in shared memory (%zu bytes)",
+                         tile.ring, R.slot_bytes, tile.groups, cap);
+    cudaError_t err = class_prepare(c, dtype, stage, true, R.total);
+    if (err != cudaSuccess) return cuda_error(err, "cudaFuncSetAttribute");
+    int bps = 0;
+    err = class_occupancy(c, dtype, stage, true, block, R.total, &bps);
+    if (err != cudaSuccess) return cuda_error(err, "occupancy query");
+    if (bps < 1) return set_error(LPDEC_EINVAL, "ring tile does not fit on an SM (%d threads, %zu bytes)", block, R.total);
+    const long long need = ((long long)n_frames + tile.groups - 1) / tile.groups;
+    const long long persistent = (long long)bps * device_sm_count(c->device);
+    lc->grid = (int)std::max<long long>(1, std::min(need, persistent));
+    lc->block = block;
+    lc->smem = R.total;
+    lc->stream = stream;
+    lc->slice_base = stage ? (int)base : 0;
+    lc->ring_slots = tile.ring;
+    lc->ring_slot_bytes = (int)R.slot_bytes;
+    lc->ring_off_slots = (int)R.off_slots;
+    lc->ring_off_scratch = (int)R.off_scratch;
+    lc->ring_off_meta = (int)R.off_meta;
+    if (layout) *layout = R.scratch;
+    return LPDEC_OK;
+}
+
+void apply_plan(DecodeArgs &a, const Tile &tile, const LaunchCfg &lc, const SliceLayout &L) {
+    a.group_threads = tile.group_threads;
+    a.smem_per_group = (int)L.bytes;
+    a.off_x = (int)L.off_x;
+    a.off_red = (int)L.off_red;
+    a.slice_base = lc.slice_base;
+    a.ring_slots = lc.ring_slots;
+    a.ring_groups = lc.ring_slots > 0 ? tile.groups : 0;
+    a.ring_slot_bytes = lc.ring_slot_bytes;
+    a.ring_off_slots = lc.ring_off_slots;
+    a.ring_off_scratch = lc.ring_off_scratch;
+    a.ring_off_meta = lc.ring_off_meta;
+}
+
 int plan_launch(const lpdec_code *c, int dtype, const Tile &tile, int n_frames, cudaStream_t stream,
                 LaunchCfg *lc, SliceLayout *layout) {
+    *lc = LaunchCfg();
+    if (tile.ring > 0) return plan_ring(c, dtype, tile, n_frames, stream, lc, layout);
     const SliceLayout L = slice_layout(c, dtype, tile.group_threads);
     size_t smem = L.bytes * (size_t)tile.groups;
     if ((int)smem > device_smem_optin(c->device) || tile.groups < 1)
@@ -398,10 +478,10 @@ int plan_launch(const lpdec_code *c, int dtype, const Tile &tile, int n_frames, 
         smem += idx_aligned;
     }
     const bool stage = lc->slice_base > 0;
-    cudaError_t err = class_prepare(c, dtype, stage, smem);
+    cudaError_t err = class_prepare(c, dtype, stage, false, smem);
     if (err != cudaSuccess) return cuda_error(err, "cudaFuncSetAttribute");
     int bps = 0;
-    err = class_occupancy(c, dtype, stage, block, smem, &bps);
+    err = class_occupancy(c, dtype, stage, false, block, smem, &bps);
     if (err != cudaSuccess) return cuda_error(err, "occupancy query");
     if (bps < 1) return set_error(LPDEC_EINVAL, "tile does not fit on an SM (%d threads, %zu bytes)", block, smem);
     const long long need = ((long long)n_frames + tile.groups - 1) / tile.groups;
@@ -485,6 +565,7 @@ int enqueue_decode(const lpdec_code *c, int n_frames, const float *llr, const lp
                    uint8_t *bits_out, int32_t *iters_out, uint8_t *cert_out, cudaStream_t stream, void *work,
                    int schedule, const Tile &tile_in, int *launches_out) {
     Tile tile = tile_in;
+    if (schedule != LPDEC_SCHED_STREAMED) tile.ring = 0;  // the ring streams parked state
     LaunchCfg lc;
     SliceLayout L;
     int rc = plan_launch(c, p->state_dtype, tile, n_frames, stream, &lc, &L);
@@ -499,11 +580,7 @@ int enqueue_decode(const lpdec_code *c, int n_frames, const float *llr, const lp
     a.bits_out = bits_out;
     a.iters_out = iters_out;
     a.cert_out = cert_out;
-    a.group_threads = tile.group_threads;
-    a.smem_per_group = (int)L.bytes;
-    a.off_x = (int)L.off_x;
-    a.off_red = (int)L.off_red;
-    a.slice_base = lc.slice_base;
+    apply_plan(a, tile, lc, L);
     const int ipl = schedule == LPDEC_SCHED_STREAMED ? p->iters_per_launch : p->max_iter;
     const int launches = schedule == LPDEC_SCHED_STREAMED ? (p->max_iter + ipl - 1) / ipl : 1;
     char *w = static_cast<char *>(work);
@@ -531,16 +608,14 @@ int enqueue_decode(const lpdec_code *c, int n_frames, const float *llr, const lp
 
 // Plan and launch the decode kernel once with caller-filled arguments (frame
 // buffers, state, queue, frame list); fills the tile fields of `a`.
-int launch_once(const lpdec_code *c, int dtype, const Tile &tile, DecodeArgs &a, cudaStream_t stream) {
+int launch_once(const lpdec_code *c, int dtype, const Tile &tile_in, DecodeArgs &a, cudaStream_t stream) {
+    Tile tile = tile_in;
+    if (!a.k_state) tile.ring = 0;  // the ring streams parked state
     LaunchCfg lc;
     SliceLayout L;
     int rc = plan_launch(c, dtype, tile, a.n_frames, stream, &lc, &L);
     if (rc) return rc;
-    a.group_threads = tile.group_threads;
-    a.smem_per_group = (int)L.bytes;
-    a.off_x = (int)L.off_x;
-    a.off_red = (int)L.off_red;
-    a.slice_base = lc.slice_base;
+    apply_plan(a, tile, lc, L);
     cudaError_t err = class_launch(c, dtype, a, lc);
     if (err != cudaSuccess) return cuda_error(err, "decode kernel launch");
     return LPDEC_OK;
@@ -651,6 +726,26 @@ extern "C" int lpdec_autotune(lpdec_code *c, const lpdec_params *p, int32_t n_fr
             if (!dup) cand.push_back(t);
         }
     }
+    if (streamed) {
+        // Ring tiles: G groups and a producer warp, R = G+1 .. G+4 slots, and
+        // the most slots that fit.
+        const size_t plain = cand.size();
+        for (size_t i = 0; i < plain; ++i) {
+            lpdec::Tile t = cand[i];
+            if (t.groups * t.group_threads + 32 > maxT) continue;
+            int last_fit = 0;
+            for (int r = t.groups + 1; r <= 64; ++r) {
+                t.ring = r;
+                if (lpdec::ring_smem_bytes(c, q.state_dtype, t, false) > (size_t)cap) break;
+                last_fit = r;
+                if (r <= t.groups + 4) cand.push_back(t);
+            }
+            if (last_fit > t.groups + 4) {
+                t.ring = last_fit;
+                cand.push_back(t);
+            }
+        }
+    }
     if (cand.empty()) return set_error(LPDEC_EINVAL, "lpdec_autotune: no tile fits this code");
     const size_t nx = (size_t)n_frames * c->n;
     char *buf = nullptr;
@@ -724,31 +819,44 @@ extern "C" int lpdec_set_tile(lpdec_code *c, int32_t state_dtype, int32_t group_
     return LPDEC_OK;
 }
 
-extern "C" int lpdec_set_streamed_tile(lpdec_code *c, int32_t state_dtype, int32_t group_threads, int32_t groups) {
+extern "C" int lpdec_set_streamed_tile(lpdec_code *c, int32_t state_dtype, int32_t group_threads, int32_t groups,
+                                       int32_t ring_slots) {
     if (!c) return set_error(LPDEC_EINVAL, "lpdec_set_streamed_tile: code is NULL");
     if (state_dtype < 0 || state_dtype > 2) return set_error(LPDEC_EINVAL, "lpdec_set_streamed_tile: unknown state_dtype");
-    if (group_threads == 0 && groups == 0) {
+    if (group_threads == 0 && groups == 0 && ring_slots == 0) {
         c->tuned_streamed[state_dtype] = lpdec::Tile();
         return LPDEC_OK;
     }
     const int maxT = lpdec::class_max_threads(c->cls);
-    if (group_threads < 32 || group_threads % 32 || groups < 1 || groups > 15 || group_threads * groups > maxT)
+    const int producer = ring_slots > 0 ? 32 : 0;
+    if (group_threads < 32 || group_threads % 32 || groups < 1 || groups > 15 ||
+        group_threads * groups + producer > maxT)
         return set_error(LPDEC_EINVAL, "lpdec_set_streamed_tile: %d groups x %d threads is not a valid tile", groups,
                          group_threads);
-    const lpdec::SliceLayout L = lpdec::slice_layout(c, state_dtype, group_threads);
-    if ((int)(L.bytes * groups) > lpdec::device_smem_optin(c->device))
-        return set_error(LPDEC_EINVAL, "lpdec_set_streamed_tile: %d slices of %zu bytes exceed shared memory", groups,
-                         L.bytes);
     lpdec::Tile t;
     t.group_threads = group_threads;
     t.groups = groups;
+    t.ring = ring_slots;
     t.valid = true;
+    if (ring_slots != 0) {
+        if (ring_slots <= groups || ring_slots > 64)
+            return set_error(LPDEC_EINVAL, "lpdec_set_streamed_tile: ring_slots=%d must be in (groups, 64]", ring_slots);
+        const size_t need = lpdec::ring_smem_bytes(c, state_dtype, t, false);
+        if (need > (size_t)lpdec::device_smem_optin(c->device))
+            return set_error(LPDEC_EINVAL, "lpdec_set_streamed_tile: a ring of %d slots needs %zu bytes of shared memory",
+                             ring_slots, need);
+    } else {
+        const lpdec::SliceLayout L = lpdec::slice_layout(c, state_dtype, group_threads);
+        if ((int)(L.bytes * groups) > lpdec::device_smem_optin(c->device))
+            return set_error(LPDEC_EINVAL, "lpdec_set_streamed_tile: %d slices of %zu bytes exceed shared memory",
+                             groups, L.bytes);
+    }
     c->tuned_streamed[state_dtype] = t;
     return LPDEC_OK;
 }
 
 extern "C" int lpdec_get_tile(const lpdec_code *c, int32_t state_dtype, int32_t schedule, int32_t *group_threads,
-                              int32_t *groups) {
+                              int32_t *groups, int32_t *ring_slots) {
     if (!c) return set_error(LPDEC_EINVAL, "lpdec_get_tile: code is NULL");
     if (state_dtype < 0 || state_dtype > 2) return set_error(LPDEC_EINVAL, "lpdec_get_tile: unknown state_dtype");
     if (schedule < 0 || schedule > 2) return set_error(LPDEC_EINVAL, "lpdec_get_tile: unknown schedule");
@@ -759,6 +867,7 @@ extern "C" int lpdec_get_tile(const lpdec_code *c, int32_t state_dtype, int32_t 
     const lpdec::Tile t = lpdec::chosen_tile(c, &p);
     if (group_threads) *group_threads = t.group_threads;
     if (groups) *groups = t.groups;
+    if (ring_slots) *ring_slots = schedule == LPDEC_SCHED_RESIDENT ? 0 : t.ring;
     return LPDEC_OK;
 }
 

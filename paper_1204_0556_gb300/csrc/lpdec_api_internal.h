@@ -15,6 +15,7 @@ namespace lpdec {
 struct Tile {
     int groups = 1;
     int group_threads = 32;
+    int ring = 0;        // STREAMED only: state slots of the producer-warp ring (0: plain kernel)
     bool valid = false;  // set when chosen by the autotuner or by hand
 };
 
@@ -35,8 +36,14 @@ Tile default_tile(const lpdec_code *c, int dtype, int max_threads = 0);
 Tile chosen_tile(const lpdec_code *c, const lpdec_params *p);
 int device_smem_optin(int device);
 int device_sm_count(int device);
+// Fills lc and (plain kernel) the slice layout or (ring kernel) the layout of
+// a group's scratch; a ring tile needs STREAMED state (k_state != null).
 int plan_launch(const lpdec_code *c, int dtype, const Tile &tile, int n_frames, cudaStream_t stream,
                 LaunchCfg *lc, SliceLayout *layout);
+// Copies the tile, layout and launch geometry into the kernel arguments.
+void apply_plan(DecodeArgs &a, const Tile &tile, const LaunchCfg &lc, const SliceLayout &L);
+// Shared memory a ring tile needs (0 if it is not a valid ring tile).
+size_t ring_smem_bytes(const lpdec_code *c, int dtype, const Tile &tile, bool stage);
 int resolve_schedule(const lpdec_code *c, const lpdec_params *p, const Tile &tile);
 size_t workspace_bytes(const lpdec_code *c, int n_frames, int schedule, int dtype, int max_iter, int ipl);
 int launch_once(const lpdec_code *c, int dtype, const Tile &tile, DecodeArgs &a, cudaStream_t stream);

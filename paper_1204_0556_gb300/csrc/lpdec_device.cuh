@@ -287,6 +287,12 @@ struct DecodeArgs {
     int off_red;             // byte offset of the reduction scratch in a slice
     int slice_base;          // byte offset of the first slice: 0, or (staged regular form) the
                              // 128-aligned size of the 16-bit index block copied to offset 0
+    // STREAMED ring (decode_kernel_ring): R state slots for G compute groups;
+    // smem_per_group / off_red then describe a group's scratch (x at 0).
+    int ring_slots;          // R (0: not a ring launch)
+    int ring_groups;         // G
+    int ring_slot_bytes;     // bytes of one slot (w then lambda/mu), a multiple of 128
+    int ring_off_slots, ring_off_scratch, ring_off_meta;
 };
 
 // Named barrier for one group (ids 1..15; id 0 is __syncthreads).
@@ -611,6 +617,9 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
@@ -675,7 +684,9 @@ struct FrameIO {
 
 // L = 1: one thread per check; L > 1: L lanes per check (segmented update).
 // Returns false only if a bulk copy timed out; the group must then stop.
-template <int D, int L, int DV, typename S>
+// READY (STREAMED ring): a parked frame's state is already in sm (the caller
+// waited for its copies), so no copy is issued or awaited here.
+template <int D, int L, int DV, typename S, bool READY = false>
 __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, int iters_this_launch, const FrameIO &io,
                           const Slice<S> &sm, int t, int T, int bar, uint32_t &phase) {
     const int lane = t & 31, w = t >> 5, nw = T >> 5;
@@ -709,7 +720,7 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
             }
             return true;
         }
-    } else {
+    } else if constexpr (!READY) {
         // STREAMED: bring the parked w and lambda/mu back with two bulk copies.
         const void *zg = io.w_state;
         const void *lg = io.l_state;
@@ -938,6 +949,193 @@ __global__ void __launch_bounds__(MAXT, 1) decode_kernel(const DecodeArgs a) {
         const int f = a.frame_list ? a.frame_list[q] : q;
         const FrameIO io = frame_io<S>(a, f);
         if (!frame_run<D, L, DV, S>(cv, a.cfg, a.iters_this_launch, io, sm, t, T, bar, phase)) break;
+    }
+    if (t == 0) bulk_wait_all();
+}
+
+// ---------------------------------------------------------------------------
+// STREAMED schedule with a producer warp and a ring of state slots.
+//
+// The CTA holds G compute groups and one producer warp.  The producer claims
+// frames from the launch's work queue in order and, for each, waits until the
+// next of R > G ring slots is free, then starts the bulk copies of the frame's
+// parked w and lambda/mu into it (or, for a frame's first launch, publishes it
+// at once).  Compute groups take slots in sequence order, wait for the slot's
+// copies, run the frame's iterations (frame_run, READY), park it from the slot
+// and release the slot once the parking copies have read it.  The loads of the
+// next R - G frames are thus in flight while the groups compute.  The producer
+// ends with one sentinel slot per group.  Every wait is bounded; a group whose
+// wait runs out reports its frame as abandoned (after a bounded wait for the
+// copies in flight) and stops, and a producer whose wait runs out drains its
+// copies and stops.
+struct RingMeta {
+    uint64_t full;   // phase k completes when the slot's k-th frame is ready
+    uint64_t empty;  // phase k completes when the slot's k-th frame is released
+    int frame;       // frame id of the slot's current sequence number, or -1 (no more frames)
+    int seq;         // that sequence number
+    int pad[2];
+};
+
+template <typename S>
+__device__ __forceinline__ S *ring_slot(const DecodeArgs &a, unsigned char *smem_raw, int s) {
+    return reinterpret_cast<S *>(smem_raw + a.ring_off_slots + (size_t)s * a.ring_slot_bytes);
+}
+
+constexpr int kRingClaim = 4;  // frames the producer claims per atomic while many remain
+
+// Publish frame f (k iterations done; f < 0: no more frames) as sequence
+// number seq of the ring: wait until its slot is free, then start the bulk
+// copies of the parked state (k > 0) or mark the slot ready at once.  Run by
+// one thread; false if the wait for the slot ran out or a group stopped.
+template <typename S>
+__device__ __forceinline__ bool ring_publish(const DecodeArgs &a, unsigned char *smem_raw, RingMeta *meta,
+                                             volatile int *abort_flag, int seq, int f, int k) {
+    const int R = a.ring_slots;
+    const int s = seq % R;
+    if (seq >= R && !mbar_wait_bounded(&meta[s].empty, (uint32_t)(seq / R - 1) & 1u)) {
+        *abort_flag = 1;
+        return false;
+    }
+    if (*abort_flag) return false;
+    meta[s].frame = f;
+    meta[s].seq = seq;
+    if (f >= 0 && k > 0) {
+        const uint32_t sbytes = (uint32_t)((size_t)a.code.Ep * sizeof(S));
+        const size_t off = (size_t)f * sbytes;
+        S *w = ring_slot<S>(a, smem_raw, s);
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&meta[s].full, 2u * sbytes);
+        bulk_load(w, reinterpret_cast<const char *>(a.w_state) + off, sbytes, &meta[s].full);
+        bulk_load(w + a.code.Ep, reinterpret_cast<const char *>(a.l_state) + off, sbytes, &meta[s].full);
+    } else {
+        mbar_arrive(&meta[s].full);
+    }
+    return true;
+}
+
+// The producer warp: claims frames in batches (one atomic per batch, the
+// batch's iteration counts read by its lanes at once), publishes those not
+// finished in order, then one sentinel per group.  Near the end of the queue
+// it claims one frame at a time, so no CTA holds a batch while others idle.
+template <typename S>
+__device__ void ring_produce(const DecodeArgs &a, unsigned char *smem_raw, RingMeta *meta, volatile int *abort_flag,
+                             int lane) {
+    const unsigned full = 0xffffffffu;
+    const int R = a.ring_slots, G = a.ring_groups;
+    int seq = 0, batch = kRingClaim, ok = 1;
+    for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(a.queue, batch);
+        base = __shfl_sync(full, base, 0);
+        if (base >= a.n_frames) break;
+        const int nb = batch;
+        batch = a.n_frames - base > 2 * (int)gridDim.x * kRingClaim ? kRingClaim : 1;
+        int f = -1, k = -1;
+        if (lane < nb && base + lane < a.n_frames) {
+            f = a.frame_list ? a.frame_list[base + lane] : base + lane;
+            k = a.k_state[f];
+        }
+        unsigned live = __ballot_sync(full, k >= 0);
+        while (live && ok) {
+            const int src = __ffs(live) - 1;
+            live &= live - 1;
+            const int fs = __shfl_sync(full, f, src);
+            const int ks = __shfl_sync(full, k, src);
+            if (lane == 0) ok = ring_publish<S>(a, smem_raw, meta, abort_flag, seq, fs, ks) ? 1 : 0;
+            ok = __shfl_sync(full, ok, 0);
+            seq += ok;
+        }
+        if (!ok) break;
+    }
+    if (lane != 0) return;
+    for (int i = 0; i < G && ok; ++i) {  // one "no more frames" slot per group
+        ok = ring_publish<S>(a, smem_raw, meta, abort_flag, seq, -1, 0) ? 1 : 0;
+        seq += ok;
+    }
+    // After a stop, the copies of the last R published slots may be in flight:
+    // wait for them (bounded) before the CTA can exit.
+    if (!ok)
+        for (int j = seq > R ? seq - R : 0; j < seq; ++j) mbar_wait_bounded(&meta[j % R].full, (uint32_t)(j / R) & 1u);
+}
+
+template <int D, int L, int DV, typename S, int MAXT, bool STAGE>
+__global__ void __launch_bounds__(MAXT, 1) decode_kernel_ring(const DecodeArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    static_assert(!STAGE || DV > 0, "index staging is built for the regular form");
+    CodeView cv = a.code;
+    if constexpr (STAGE) {
+        copy16(smem_raw, a.code.col16, a.code.idx16_bytes, threadIdx.x, blockDim.x);
+        cv.col16 = reinterpret_cast<const uint16_t *>(smem_raw);
+        cv.csc16 = cv.col16 + a.code.col16_elems;
+    }
+    const int R = a.ring_slots, T = a.group_threads;
+    RingMeta *meta = reinterpret_cast<RingMeta *>(smem_raw + a.ring_off_meta);
+    int *ctr = reinterpret_cast<int *>(meta + R);  // [0] consumer sequence counter, [1] stop flag
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < R; ++s) {
+            mbar_init(&meta[s].full, 1);
+            mbar_init(&meta[s].empty, 1);
+            meta[s].frame = -1;
+            meta[s].seq = -1;
+        }
+        ctr[0] = 0;
+        ctr[1] = 0;
+        fence_proxy_async_smem();
+    }
+    __syncthreads();
+    volatile int *abort_flag = ctr + 1;
+    if ((int)threadIdx.x >= a.ring_groups * T) {  // the producer warp
+        ring_produce<S>(a, smem_raw, meta, abort_flag, threadIdx.x & 31);
+        return;
+    }
+    const int g = threadIdx.x / T;
+    const int t = threadIdx.x - g * T;
+    const int bar = 1 + g;
+    unsigned char *scr = smem_raw + a.ring_off_scratch + (size_t)g * a.smem_per_group;
+    Slice<S> sm;
+    sm.x = reinterpret_cast<float *>(scr);
+    sm.red = reinterpret_cast<float *>(scr + a.off_red);
+    sm.flags = reinterpret_cast<int *>(sm.red + 2 * (T >> 5));
+    sm.mbar = nullptr;
+    uint32_t unused_phase = 0;
+    int par = 0;
+    for (;;) {
+        if (t == 0) sm.flags[4 + par] = atomicAdd(&ctr[0], 1);
+        group_sync(bar, T);
+        const int my = sm.flags[4 + par];
+        par ^= 1;
+        const int s = my % R;
+        const uint32_t ph = (uint32_t)(my / R) & 1u;
+        if (t == 0) sm.flags[3] = mbar_wait_bounded(&meta[s].full, ph) ? 1 : 0;
+        group_sync(bar, T);
+        if (sm.flags[3] == 0) {
+            if (t == 0) {
+                *abort_flag = 1;
+                if (meta[s].seq == my && meta[s].frame >= 0) {  // published, copies late
+                    mbar_wait_bounded(&meta[s].full, ph);
+                    const int f = meta[s].frame;
+                    if (a.iters_out) a.iters_out[f] = kFrameTimeout;
+                    if (a.cert_out) a.cert_out[f] = 0;
+                    a.k_state[f] = -1;
+                }
+            }
+            break;
+        }
+        mbar_wait_bounded(&meta[s].full, ph);  // complete: every thread acquires the slot
+        const int f = meta[s].frame;
+        if (f < 0) break;  // no more frames
+        sm.w = ring_slot<S>(a, smem_raw, s);
+        sm.l = sm.w + a.code.Ep;
+        const FrameIO io = frame_io<S>(a, f);
+        frame_run<D, L, DV, S, true>(cv, a.cfg, a.iters_this_launch, io, sm, t, T, bar, unused_phase);
+        if (t == 0) {
+            // the group's writes to the slot (ordered by its last barrier) and
+            // the parking copies' reads of it are done before the producer
+            // starts the next copies into it
+            fence_proxy_async_smem();
+            bulk_wait_read_all();
+            mbar_arrive(&meta[s].empty);
+        }
     }
     if (t == 0) bulk_wait_all();
 }

@@ -46,6 +46,9 @@ struct LaunchCfg {
     cudaStream_t stream;
     int slice_base = 0;  // staged regular form: shared-memory offset of the first slice (after the
                          // 16-bit index block at offset 0); 0 when the indices are not staged
+    // ring kernel (STREAMED): slots, slot size and the offsets of the slots,
+    // the groups' scratch and the slot metadata; ring_slots = 0 otherwise
+    int ring_slots = 0, ring_slot_bytes = 0, ring_off_slots = 0, ring_off_scratch = 0, ring_off_meta = 0;
 };
 
 // Per-class entry points, defined in lpdec_kD.cu.
@@ -53,9 +56,9 @@ struct LaunchCfg {
 // exactly D (selects the regular-code kernel where one is built), else 0.
 #define LPDEC_DECLARE_CLASS(D)                                                                           \
     cudaError_t launch_decode_##D(int dtype, int reg_dv, const DecodeArgs &a, const LaunchCfg &lc);      \
-    cudaError_t occupancy_decode_##D(int dtype, int reg_dv, bool stage, int block, size_t smem,            \
+    cudaError_t occupancy_decode_##D(int dtype, int reg_dv, bool stage, bool ring, int block, size_t smem, \
                                      int *blocks_per_sm);                                                 \
-    cudaError_t prepare_decode_##D(int dtype, int reg_dv, bool stage, size_t smem);                      \
+    cudaError_t prepare_decode_##D(int dtype, int reg_dv, bool stage, bool ring, size_t smem);           \
     cudaError_t launch_project_##D(int d, long long count, const float *v, float *z, cudaStream_t s);
 LPDEC_DECLARE_CLASS(6)
 LPDEC_DECLARE_CLASS(8)

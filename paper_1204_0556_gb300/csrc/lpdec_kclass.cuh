@@ -24,41 +24,54 @@ constexpr int kMaxT = class_max_threads_D(kD);
 constexpr int kRegDV = kD == 8 ? 4 : 3;
 
 // Kernel forms of this class: 0 generic, 1 regular (indices from global
-// memory), 2 regular with the indices staged in shared memory.
-constexpr int kForms = 3;
+// memory), 2 regular with the indices staged in shared memory; 3-5 the same
+// three as STREAMED ring kernels (decode_kernel_ring).
+constexpr int kForms = 6;
 
-template <int DV, bool STAGE, typename S>
+template <int DV, bool STAGE, bool RING, typename S>
 const void *decode_fn() {
-    return reinterpret_cast<const void *>(&decode_kernel<kD, kL, DV, S, kMaxT, STAGE>);
+    if constexpr (RING) return reinterpret_cast<const void *>(&decode_kernel_ring<kD, kL, DV, S, kMaxT, STAGE>);
+    else return reinterpret_cast<const void *>(&decode_kernel<kD, kL, DV, S, kMaxT, STAGE>);
 }
 
-template <int DV, bool STAGE>
+template <int DV, bool STAGE, bool RING>
 const void *decode_fn_dtype(int dtype) {
     switch (dtype) {
-        case 0: return decode_fn<DV, STAGE, float>();
-        case 1: return decode_fn<DV, STAGE, __nv_bfloat16>();
-        case 2: return decode_fn<DV, STAGE, __half>();
+        case 0: return decode_fn<DV, STAGE, RING, float>();
+        case 1: return decode_fn<DV, STAGE, RING, __nv_bfloat16>();
+        case 2: return decode_fn<DV, STAGE, RING, __half>();
         default: return nullptr;
     }
 }
 
-int form_of(int reg_dv, bool stage) {
-    if (kRegDV > 0 && reg_dv == kRegDV) return stage ? 2 : 1;
-    return 0;
+int form_of(int reg_dv, bool stage, bool ring) {
+    const int f = (kRegDV > 0 && reg_dv == kRegDV) ? (stage ? 2 : 1) : 0;
+    return ring ? f + 3 : f;
 }
 
 const void *decode_fn_for(int dtype, int form) {
-    if (form == 2) return decode_fn_dtype<kRegDV, true>(dtype);
-    if (form == 1) return decode_fn_dtype<kRegDV, false>(dtype);
-    return decode_fn_dtype<0, false>(dtype);
+    switch (form) {
+        case 5: return decode_fn_dtype<kRegDV, true, true>(dtype);
+        case 4: return decode_fn_dtype<kRegDV, false, true>(dtype);
+        case 3: return decode_fn_dtype<0, false, true>(dtype);
+        case 2: return decode_fn_dtype<kRegDV, true, false>(dtype);
+        case 1: return decode_fn_dtype<kRegDV, false, false>(dtype);
+        default: return decode_fn_dtype<0, false, false>(dtype);
+    }
 }
 
-template <int DV, bool STAGE>
+template <int DV, bool STAGE, bool RING, typename S>
+void launch_one(const DecodeArgs &a, const LaunchCfg &lc) {
+    if constexpr (RING) decode_kernel_ring<kD, kL, DV, S, kMaxT, STAGE><<<lc.grid, lc.block, lc.smem, lc.stream>>>(a);
+    else decode_kernel<kD, kL, DV, S, kMaxT, STAGE><<<lc.grid, lc.block, lc.smem, lc.stream>>>(a);
+}
+
+template <int DV, bool STAGE, bool RING>
 cudaError_t launch_dv(int dtype, const DecodeArgs &a, const LaunchCfg &lc) {
     switch (dtype) {
-        case 0: decode_kernel<kD, kL, DV, float, kMaxT, STAGE><<<lc.grid, lc.block, lc.smem, lc.stream>>>(a); break;
-        case 1: decode_kernel<kD, kL, DV, __nv_bfloat16, kMaxT, STAGE><<<lc.grid, lc.block, lc.smem, lc.stream>>>(a); break;
-        case 2: decode_kernel<kD, kL, DV, __half, kMaxT, STAGE><<<lc.grid, lc.block, lc.smem, lc.stream>>>(a); break;
+        case 0: launch_one<DV, STAGE, RING, float>(a, lc); break;
+        case 1: launch_one<DV, STAGE, RING, __nv_bfloat16>(a, lc); break;
+        case 2: launch_one<DV, STAGE, RING, __half>(a, lc); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -71,8 +84,8 @@ cudaError_t launch_dv(int dtype, const DecodeArgs &a, const LaunchCfg &lc) {
 // calls.  Per device: a kernel attribute is per device.
 static std::atomic<int> g_smem_granted[64][3][kForms];
 
-cudaError_t LPDEC_CAT(prepare_decode_, LPDEC_D)(int dtype, int reg_dv, bool stage, size_t smem) {
-    const int form = form_of(reg_dv, stage);
+cudaError_t LPDEC_CAT(prepare_decode_, LPDEC_D)(int dtype, int reg_dv, bool stage, bool ring, size_t smem) {
+    const int form = form_of(reg_dv, stage, ring);
     const void *fn = decode_fn_for(dtype, form);
     if (!fn) return cudaErrorInvalidValue;
     int dev = 0;
@@ -90,19 +103,25 @@ cudaError_t LPDEC_CAT(prepare_decode_, LPDEC_D)(int dtype, int reg_dv, bool stag
     return err;
 }
 
-cudaError_t LPDEC_CAT(occupancy_decode_, LPDEC_D)(int dtype, int reg_dv, bool stage, int block, size_t smem,
-                                                   int *blocks_per_sm) {
-    const void *fn = decode_fn_for(dtype, form_of(reg_dv, stage));
+cudaError_t LPDEC_CAT(occupancy_decode_, LPDEC_D)(int dtype, int reg_dv, bool stage, bool ring, int block,
+                                                   size_t smem, int *blocks_per_sm) {
+    const void *fn = decode_fn_for(dtype, form_of(reg_dv, stage, ring));
     if (!fn) return cudaErrorInvalidValue;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, block, smem);
 }
 
 cudaError_t LPDEC_CAT(launch_decode_, LPDEC_D)(int dtype, int reg_dv, const DecodeArgs &a, const LaunchCfg &lc) {
     if (lc.block > kMaxT) return cudaErrorInvalidConfiguration;
-    const int form = form_of(reg_dv, a.slice_base > 0);
-    if (form == 2) return launch_dv<kRegDV, true>(dtype, a, lc);
-    if (form == 1) return launch_dv<kRegDV, false>(dtype, a, lc);
-    return launch_dv<0, false>(dtype, a, lc);
+    const bool ring = a.ring_slots > 0;
+    if (ring && !a.k_state) return cudaErrorInvalidValue;  // the ring streams parked state
+    switch (form_of(reg_dv, a.slice_base > 0, ring)) {
+        case 5: return launch_dv<kRegDV, true, true>(dtype, a, lc);
+        case 4: return launch_dv<kRegDV, false, true>(dtype, a, lc);
+        case 3: return launch_dv<0, false, true>(dtype, a, lc);
+        case 2: return launch_dv<kRegDV, true, false>(dtype, a, lc);
+        case 1: return launch_dv<kRegDV, false, false>(dtype, a, lc);
+        default: return launch_dv<0, false, false>(dtype, a, lc);
+    }
 }
 
 cudaError_t LPDEC_CAT(launch_project_, LPDEC_D)(int d, long long count, const float *v, float *z,

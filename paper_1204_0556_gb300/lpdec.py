@@ -116,8 +116,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
             "lpdec_mixed_plan_destroy": (ctypes.c_int, [_vp]),
             "lpdec_decode_dual": (ctypes.c_int, [_vp, _i32, _vp, ctypes.c_double, _i32, _vp, _vp, _vp, _vp, _vp]),
             "lpdec_dual_set_tile": (ctypes.c_int, [_vp, _i32, _i32]),
-            "lpdec_set_streamed_tile": (ctypes.c_int, [_vp, _i32, _i32, _i32]),
-            "lpdec_get_tile": (ctypes.c_int, [_vp, _i32, _i32, _i32p, _i32p]),
+            "lpdec_set_streamed_tile": (ctypes.c_int, [_vp, _i32, _i32, _i32, _i32]),
+            "lpdec_get_tile": (ctypes.c_int, [_vp, _i32, _i32, _i32p, _i32p, _i32p]),
         })
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -247,21 +247,25 @@ def lpdec_autotune(handle: int, params, n_frames: int, llr_ptr: int, stream_ptr:
     ms = ctypes.c_double()
     _check(load().lpdec_autotune(handle, ctypes.byref(params), n_frames, llr_ptr, stream_ptr, ctypes.byref(gt),
                                  ctypes.byref(g), ctypes.byref(ms)))
-    return {"group_threads": gt.value, "groups": g.value, "ms_per_frame": ms.value}
+    ring = 0
+    if params.schedule == SCHED_STREAMED:
+        ring = lpdec_get_tile(handle, params.state_dtype, SCHED_STREAMED)["ring_slots"]
+    return {"group_threads": gt.value, "groups": g.value, "ring_slots": ring, "ms_per_frame": ms.value}
 
 
 def lpdec_set_tile(handle: int, state_dtype: int, group_threads: int, groups: int) -> None:
     _check(load().lpdec_set_tile(handle, state_dtype, group_threads, groups))
 
 
-def lpdec_set_streamed_tile(handle: int, state_dtype: int, group_threads: int, groups: int) -> None:
-    _check(load().lpdec_set_streamed_tile(handle, state_dtype, group_threads, groups))
+def lpdec_set_streamed_tile(handle: int, state_dtype: int, group_threads: int, groups: int,
+                            ring_slots: int = 0) -> None:
+    _check(load().lpdec_set_streamed_tile(handle, state_dtype, group_threads, groups, ring_slots))
 
 
 def lpdec_get_tile(handle: int, state_dtype: int, schedule: int) -> dict:
-    gt, g = _i32(), _i32()
-    _check(load().lpdec_get_tile(handle, state_dtype, schedule, ctypes.byref(gt), ctypes.byref(g)))
-    return {"group_threads": gt.value, "groups": g.value}
+    gt, g, r = _i32(), _i32(), _i32()
+    _check(load().lpdec_get_tile(handle, state_dtype, schedule, ctypes.byref(gt), ctypes.byref(g), ctypes.byref(r)))
+    return {"group_threads": gt.value, "groups": g.value, "ring_slots": r.value}
 
 
 def lpdec_mixed_plan_create(handles, frame_code, params) -> int:

@@ -214,7 +214,8 @@ def test_streamed_tile_equals_resident(gpu, name, state, eps):
         pr = gpu.make_params(eps=eps, max_iter=60, state=state, schedule="resident")
         a = {k: v.cpu().numpy() for k, v in gpu.decode(C, d_llr, pr).items()}
         gpu.lpdec_set_streamed_tile(C.handle, dt, T, 2 if name != "C8000" else 1)
-        assert gpu.lpdec_get_tile(C.handle, dt, gpu.SCHED_RESIDENT) == {"group_threads": T, "groups": 1}
+        assert gpu.lpdec_get_tile(C.handle, dt, gpu.SCHED_RESIDENT) == {"group_threads": T, "groups": 1,
+                                                                        "ring_slots": 0}
         assert gpu.lpdec_get_tile(C.handle, dt, gpu.SCHED_STREAMED)["group_threads"] == T
         for ipl in (1, 4):
             ps = gpu.make_params(eps=eps, max_iter=60, state=state, schedule="streamed", iters_per_launch=ipl)
@@ -247,6 +248,102 @@ def test_streamed_autotune_keeps_results(gpu, c1056):
             assert np.array_equal(a[k], b[k]), k
             assert np.array_equal(r0[k], r1[k]), k
             assert np.array_equal(a[k], r0[k]), k
+    finally:
+        C.close()
+
+
+# (code, state, eps, frames, [(groups, ring slots), ...]); the group width is
+# the RESIDENT tile's, so the stopping test's partial sums agree bit for bit.
+RING_CASES = [
+    ("C1056", "f32", 0.0, 41, [(1, 2), (3, 4), (5, 7), (2, 8)]),
+    ("C1056", "f32", 1e-5, 41, [(4, 6)]),
+    ("C1056", "bf16", 1e-5, 37, [(5, 8)]),
+    ("C1056", "f16", 0.0, 3, [(5, 7)]),  # fewer frames than groups
+    ("C4000", "f32", 0.0, 9, [(1, 2)]),
+    ("C4000", "bf16", 1e-5, 9, [(2, 3)]),
+    ("S12", "f32", 1e-5, 13, [(2, 4)]),
+    ("S16V4", "f32", 0.0, 13, [(2, 3)]),
+    ("R20", "f32", 1e-5, 17, [(3, 5)]),
+    ("C8000", "f16", 1e-5, 7, [(1, 2)]),
+]
+
+
+@pytest.mark.parametrize("name,state,eps,frames,rings", RING_CASES)
+def test_ring_equals_resident(gpu, name, state, eps, frames, rings):
+    """STREAMED with the producer-warp ring (the next frames' parked state
+    prefetched into shared-memory slots while the groups compute) gives the
+    RESIDENT outputs bit for bit: any groups and slots, any iterations per
+    launch, frames that stop early (skipped by the producer in later launches),
+    a frame with a non-finite LLR, and fewer frames than groups."""
+    import torch
+
+    code = _shape(name)
+    llr = I.awgn_llr(code, 2.5, frames, 707)
+    llr[frames // 2, 3] = np.nan
+    dt = {"f32": 0, "bf16": 1, "f16": 2}[state]
+    d_llr = torch.from_numpy(llr).cuda()
+    C = gpu.Code(code)
+    try:
+        T = {"C1056": 64, "C4000": 256, "S12": 128, "S16V4": 256, "R20": 128, "C8000": 512}[name]
+        gpu.lpdec_set_tile(C.handle, dt, T, 1)
+        pr = gpu.make_params(eps=eps, max_iter=50, state=state, schedule="resident")
+        a = {k: v.cpu().numpy() for k, v in gpu.decode(C, d_llr, pr).items()}
+        assert a["iters"][frames // 2] == -1
+        for g, r in rings:
+            gpu.lpdec_set_streamed_tile(C.handle, dt, T, g, r)
+            assert gpu.lpdec_get_tile(C.handle, dt, gpu.SCHED_STREAMED) == {"group_threads": T, "groups": g,
+                                                                            "ring_slots": r}
+            for ipl in (1, 3, 50):
+                ps = gpu.make_params(eps=eps, max_iter=50, state=state, schedule="streamed", iters_per_launch=ipl)
+                b = {k: v.cpu().numpy() for k, v in gpu.decode(C, d_llr, ps).items()}
+                for k in a:
+                    assert np.array_equal(a[k], b[k]), (g, r, ipl, k)
+    finally:
+        C.close()
+
+
+def test_ring_tile_validation(gpu, c1056):
+    """Ring tiles that cannot run are refused before any launch."""
+    C = gpu.Code(c1056)
+    try:
+        for g, r in [(3, 3), (3, 2), (1, 65), (40, 41)]:  # slots <= groups, > 64, too many threads
+            with pytest.raises(gpu.LpdecError):
+                gpu.lpdec_set_streamed_tile(C.handle, 0, 64, g, r)
+        with pytest.raises(gpu.LpdecError):  # 1056-wide groups + the producer warp exceed 1024 threads
+            gpu.lpdec_set_streamed_tile(C.handle, 0, 1024, 1, 2)
+        with pytest.raises(gpu.LpdecError):  # 64 slots of 25 KB do not fit in shared memory
+            gpu.lpdec_set_streamed_tile(C.handle, 0, 64, 1, 64)
+        gpu.lpdec_set_streamed_tile(C.handle, 0, 64, 2, 4)
+        gpu.lpdec_set_streamed_tile(C.handle, 0, 0, 0, 0)
+        assert gpu.lpdec_get_tile(C.handle, 0, gpu.SCHED_STREAMED)["ring_slots"] == 0
+    finally:
+        C.close()
+
+
+def test_streamed_autotune_with_ring_keeps_results(gpu, c1056):
+    """The STREAMED autotuner also times ring tiles; whichever it keeps, the
+    results are those of the RESIDENT schedule."""
+    import torch
+
+    llr = I.awgn_llr(c1056, 2.0, 300, 808)
+    C = gpu.Code(c1056)
+    try:
+        d_llr = torch.from_numpy(llr).cuda()
+        sp = int(torch.cuda.current_stream().cuda_stream)
+        t = gpu.lpdec_autotune(C.handle, gpu.make_params(eps=0.0, max_iter=4, schedule="streamed"), 300,
+                               d_llr.data_ptr(), sp)
+        assert t["ring_slots"] == 0 or t["ring_slots"] > t["groups"]
+        got = gpu.lpdec_get_tile(C.handle, 0, gpu.SCHED_STREAMED)
+        assert got == {k: t[k] for k in ("group_threads", "groups", "ring_slots")}
+        # the RESIDENT tile of the same group width, for the same partial sums
+        gpu.lpdec_set_tile(C.handle, 0, t["group_threads"], 1)
+        gpu.lpdec_set_streamed_tile(C.handle, 0, t["group_threads"], t["groups"], t["ring_slots"])
+        ps = gpu.make_params(eps=1e-5, max_iter=80, schedule="streamed", iters_per_launch=5)
+        pr = gpu.make_params(eps=1e-5, max_iter=80, schedule="resident")
+        a = {k: v.cpu().numpy() for k, v in gpu.decode(C, d_llr, ps).items()}
+        b = {k: v.cpu().numpy() for k, v in gpu.decode(C, d_llr, pr).items()}
+        for k in a:
+            assert np.array_equal(a[k], b[k]), k
     finally:
         C.close()
 
