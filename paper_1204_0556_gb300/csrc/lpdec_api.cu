@@ -381,16 +381,19 @@ Tile chosen_tile(const lpdec_code *c, const lpdec_params *p) {
 }
 
 // Ring kernel layout (must match decode_kernel_ring): [16-bit index block,
-// when staged] [R state slots, w then lambda/mu] [G scratch areas: x, the
-// reduction scratch and 8 ints of flags] [R slot records of 32 bytes, then two
-// ints: the consumers' sequence counter and the stop flag].
+// when staged] [R slots: w, lambda/mu, and the frame's LLR row when the slots
+// hold it] [G scratch areas: x, the reduction scratch and 8 ints of flags]
+// [R slot records of 32 bytes, then two ints: the consumers' sequence counter
+// and the stop flag].
 struct RingLayout {
-    size_t slot_bytes = 0, off_slots = 0, off_scratch = 0, off_meta = 0, total = 0;
+    size_t slot_bytes = 0, llr_off = 0, off_slots = 0, off_scratch = 0, off_meta = 0, total = 0;
     SliceLayout scratch;  // off_x = 0
 };
-static RingLayout ring_layout(const lpdec_code *c, int dtype, const Tile &tile, size_t base) {
+static RingLayout ring_layout(const lpdec_code *c, int dtype, const Tile &tile, size_t base, bool llr) {
     RingLayout R;
-    R.slot_bytes = (2 * (size_t)c->Ep * dtype_size(dtype) + 127) & ~(size_t)127;
+    const size_t state = 2 * (size_t)c->Ep * dtype_size(dtype);  // a multiple of 32
+    R.llr_off = llr ? state : 0;
+    R.slot_bytes = (state + (llr ? (size_t)c->n * 4 : 0) + 127) & ~(size_t)127;
     R.scratch.off_x = 0;
     R.scratch.off_red = ((size_t)c->n * 4 + 15) & ~(size_t)15;
     R.scratch.bytes = (R.scratch.off_red + (size_t)(tile.group_threads / 32) * 2 * 4 + 8 * 4 + 127) & ~(size_t)127;
@@ -401,10 +404,9 @@ static RingLayout ring_layout(const lpdec_code *c, int dtype, const Tile &tile, 
     return R;
 }
 
-size_t ring_smem_bytes(const lpdec_code *c, int dtype, const Tile &tile, bool stage) {
+size_t ring_smem_bytes(const lpdec_code *c, int dtype, const Tile &tile) {
     if (tile.ring <= tile.groups || tile.ring > 64) return 0;
-    const size_t base = stage ? (((size_t)c->idx16_bytes + 127) & ~(size_t)127) : 0;
-    return ring_layout(c, dtype, tile, base).total;
+    return ring_layout(c, dtype, tile, 0, false).total;
 }
 
 static int plan_ring(const lpdec_code *c, int dtype, const Tile &tile, int n_frames, cudaStream_t stream,
@@ -415,9 +417,21 @@ static int plan_ring(const lpdec_code *c, int dtype, const Tile &tile, int n_fra
         return set_error(LPDEC_EINVAL, "invalid ring tile: %d groups x %d threads, %d slots", tile.groups,
                          tile.group_threads, tile.ring);
     const size_t cap = (size_t)device_smem_optin(c->device);
-    bool stage = c->reg_dv > 0 && c->idx16_bytes > 0 && ring_smem_bytes(c, dtype, tile, true) <= cap;
-    const size_t base = stage ? (((size_t)c->idx16_bytes + 127) & ~(size_t)127) : 0;
-    const RingLayout R = ring_layout(c, dtype, tile, base);
+    // The first layout that fits, in this order: LLR rows in the slots (each
+    // launch then reads them with one bulk copy per frame instead of a load
+    // per variable; the copy needs 4n to be a multiple of 16) with and
+    // without the staged indices, then without the LLR rows.
+    const size_t idx_base = ((size_t)c->idx16_bytes + 127) & ~(size_t)127;
+    const bool can_stage = c->reg_dv > 0 && c->idx16_bytes > 0, can_llr = c->n % 4 == 0;
+    const bool opts[4][2] = {{true, true}, {false, true}, {true, false}, {false, false}};  // {stage, llr}
+    RingLayout R;
+    bool stage = false;
+    for (const auto &o : opts) {
+        if ((o[0] && !can_stage) || (o[1] && !can_llr)) continue;
+        R = ring_layout(c, dtype, tile, o[0] ? idx_base : 0, o[1]);
+        stage = o[0];
+        if (R.total <= cap) break;
+    }
     if (R.total > cap)
         return set_error(LPDEC_EINVAL, "ring of %d slots of %zu bytes and %d groups does not fit in shared memory (%zu bytes)",
                          tile.ring, R.slot_bytes, tile.groups, cap);
@@ -433,12 +447,13 @@ static int plan_ring(const lpdec_code *c, int dtype, const Tile &tile, int n_fra
     lc->block = block;
     lc->smem = R.total;
     lc->stream = stream;
-    lc->slice_base = stage ? (int)base : 0;
+    lc->slice_base = stage ? (int)idx_base : 0;
     lc->ring_slots = tile.ring;
     lc->ring_slot_bytes = (int)R.slot_bytes;
     lc->ring_off_slots = (int)R.off_slots;
     lc->ring_off_scratch = (int)R.off_scratch;
     lc->ring_off_meta = (int)R.off_meta;
+    lc->ring_llr_off = (int)R.llr_off;
     if (layout) *layout = R.scratch;
     return LPDEC_OK;
 }
@@ -455,6 +470,8 @@ void apply_plan(DecodeArgs &a, const Tile &tile, const LaunchCfg &lc, const Slic
     a.ring_off_slots = lc.ring_off_slots;
     a.ring_off_scratch = lc.ring_off_scratch;
     a.ring_off_meta = lc.ring_off_meta;
+    // the LLR rows are copied in bulk: the batch must start on a 16-byte boundary
+    a.ring_llr_off = (reinterpret_cast<uintptr_t>(a.llr) & 15) ? 0 : lc.ring_llr_off;
 }
 
 int plan_launch(const lpdec_code *c, int dtype, const Tile &tile, int n_frames, cudaStream_t stream,
@@ -736,7 +753,7 @@ extern "C" int lpdec_autotune(lpdec_code *c, const lpdec_params *p, int32_t n_fr
             int last_fit = 0;
             for (int r = t.groups + 1; r <= 64; ++r) {
                 t.ring = r;
-                if (lpdec::ring_smem_bytes(c, q.state_dtype, t, false) > (size_t)cap) break;
+                if (lpdec::ring_smem_bytes(c, q.state_dtype, t) > (size_t)cap) break;
                 last_fit = r;
                 if (r <= t.groups + 4) cand.push_back(t);
             }
@@ -841,7 +858,7 @@ extern "C" int lpdec_set_streamed_tile(lpdec_code *c, int32_t state_dtype, int32
     if (ring_slots != 0) {
         if (ring_slots <= groups || ring_slots > 64)
             return set_error(LPDEC_EINVAL, "lpdec_set_streamed_tile: ring_slots=%d must be in (groups, 64]", ring_slots);
-        const size_t need = lpdec::ring_smem_bytes(c, state_dtype, t, false);
+        const size_t need = lpdec::ring_smem_bytes(c, state_dtype, t);
         if (need > (size_t)lpdec::device_smem_optin(c->device))
             return set_error(LPDEC_EINVAL, "lpdec_set_streamed_tile: a ring of %d slots needs %zu bytes of shared memory",
                              ring_slots, need);

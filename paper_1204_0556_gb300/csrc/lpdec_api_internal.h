@@ -42,8 +42,9 @@ int plan_launch(const lpdec_code *c, int dtype, const Tile &tile, int n_frames, 
                 LaunchCfg *lc, SliceLayout *layout);
 // Copies the tile, layout and launch geometry into the kernel arguments.
 void apply_plan(DecodeArgs &a, const Tile &tile, const LaunchCfg &lc, const SliceLayout &L);
-// Shared memory a ring tile needs (0 if it is not a valid ring tile).
-size_t ring_smem_bytes(const lpdec_code *c, int dtype, const Tile &tile, bool stage);
+// Least shared memory a ring tile needs (indices not staged, slots without the
+// LLR row); 0 if it is not a valid ring tile.
+size_t ring_smem_bytes(const lpdec_code *c, int dtype, const Tile &tile);
 int resolve_schedule(const lpdec_code *c, const lpdec_params *p, const Tile &tile);
 size_t workspace_bytes(const lpdec_code *c, int n_frames, int schedule, int dtype, int max_iter, int ipl);
 int launch_once(const lpdec_code *c, int dtype, const Tile &tile, DecodeArgs &a, cudaStream_t stream);

@@ -291,8 +291,9 @@ struct DecodeArgs {
     // smem_per_group / off_red then describe a group's scratch (x at 0).
     int ring_slots;          // R (0: not a ring launch)
     int ring_groups;         // G
-    int ring_slot_bytes;     // bytes of one slot (w then lambda/mu), a multiple of 128
+    int ring_slot_bytes;     // bytes of one slot (w, lambda/mu, then the LLR row), a multiple of 128
     int ring_off_slots, ring_off_scratch, ring_off_meta;
+    int ring_llr_off;        // byte offset of the frame's LLR row in a slot; 0: LLRs read from global memory
 };
 
 // Named barrier for one group (ids 1..15; id 0 is __syncthreads).
@@ -593,7 +594,9 @@ struct Slice {
     float *x, *red;
     int *flags;      // [0] converged, [1] residual ok, [2] bad LLR, [3] copy ok, [4..5] frame ids
     uint64_t *mbar;  // flags[6..7]: completion barrier of the bulk loads
+    const float *llr = nullptr;  // ring kernel: the frame's LLRs copied into its slot (else read from io.llr)
 };
+
 
 // Copy nbytes (a multiple of 16) between 16-byte aligned buffers, cooperatively.
 __device__ __forceinline__ void copy16(void *dst, const void *src, int nbytes, int t, int T) {
@@ -634,6 +637,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// Load of shared data that no thread writes while it is read (a staged LLR
+// row): free to be reordered around shared-memory stores.
+__device__ __forceinline__ float ld_shared_ro(const float *p) {
+    float v;
+    asm("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(smem_addr(p)));
+    return v;
+}
+// LLR i of the frame: from its row copied into shared memory (ring kernel,
+// gs != null), else a read-only global load.
+template <bool READY>
+__device__ __forceinline__ float llr_at(const float *g, const float *gs, int i) {
+    if constexpr (READY)
+        if (gs) return ld_shared_ro(gs + i);
+    return __ldg(g + i);
+}
+
 // Wait for the mbarrier phase with the given parity, for at most ~1 s of SM
 // clocks; returns false on timeout (the caller reports it, never spins forever).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
@@ -692,6 +711,7 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
     const int lane = t & 31, w = t >> 5, nw = T >> 5;
     volatile int *flags = sm.flags;
     const float *gam = io.llr;
+    const float *gam_s = READY ? sm.llr : nullptr;
     const bool streamed = io.k_state != nullptr;
     const int state_bytes = c.Ep * (int)sizeof(S);
 
@@ -702,7 +722,7 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
     if (k == 0) {
         // Algorithm 1 initialization: z = lambda = 0 (w = 0).  Also reject non-finite LLRs.
         int bad = 0;
-        for (int i = t; i < c.n; i += T) bad |= !isfinite(__ldg(gam + i));
+        for (int i = t; i < c.n; i += T) bad |= !isfinite(llr_at<READY>(gam, gam_s, i));
         zero16(sm.w, 2 * state_bytes, t, T);
         bad = __any_sync(0xffffffffu, bad);
         group_sync(bar, T);
@@ -771,7 +791,7 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
                     acc += wv[s];
                 }
                 inv_dv = 1.0f / (float)DV;
-                const float gi = __ldg(gam + i);
+                const float gi = llr_at<READY>(gam, gam_s, i);
                 const float x = __saturatef((acc - gi * p.mu_inv) * inv_dv);
                 sm.x[i] = x;
                 if (fold) {
@@ -786,7 +806,7 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
                     acc += ld<S>(sm.w[e]);
                 }
                 inv_dv = __frcp_rn((float)(s1 - s0));
-                const float gi = __ldg(gam + i);
+                const float gi = llr_at<READY>(gam, gam_s, i);
                 const float x = __saturatef((acc - gi * p.mu_inv) * inv_dv);
                 sm.x[i] = x;
             }
@@ -985,8 +1005,9 @@ constexpr int kRingClaim = 4;  // frames the producer claims per atomic while ma
 
 // Publish frame f (k iterations done; f < 0: no more frames) as sequence
 // number seq of the ring: wait until its slot is free, then start the bulk
-// copies of the parked state (k > 0) or mark the slot ready at once.  Run by
-// one thread; false if the wait for the slot ran out or a group stopped.
+// copies of the parked state (k > 0) and of the frame's LLRs (when the slots
+// hold them), or mark the slot ready at once.  Run by one thread; false if the
+// wait for the slot ran out or a group stopped.
 template <typename S>
 __device__ __forceinline__ bool ring_publish(const DecodeArgs &a, unsigned char *smem_raw, RingMeta *meta,
                                              volatile int *abort_flag, int seq, int f, int k) {
@@ -999,14 +1020,21 @@ __device__ __forceinline__ bool ring_publish(const DecodeArgs &a, unsigned char 
     if (*abort_flag) return false;
     meta[s].frame = f;
     meta[s].seq = seq;
-    if (f >= 0 && k > 0) {
-        const uint32_t sbytes = (uint32_t)((size_t)a.code.Ep * sizeof(S));
-        const size_t off = (size_t)f * sbytes;
+    const uint32_t sbytes = (uint32_t)((size_t)a.code.Ep * sizeof(S));
+    const uint32_t lbytes = a.ring_llr_off ? (uint32_t)a.code.n * 4u : 0u;  // a multiple of 16 (host checks)
+    const uint32_t tx = f < 0 ? 0u : (k > 0 ? 2u * sbytes : 0u) + lbytes;
+    if (tx) {
         S *w = ring_slot<S>(a, smem_raw, s);
         fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&meta[s].full, 2u * sbytes);
-        bulk_load(w, reinterpret_cast<const char *>(a.w_state) + off, sbytes, &meta[s].full);
-        bulk_load(w + a.code.Ep, reinterpret_cast<const char *>(a.l_state) + off, sbytes, &meta[s].full);
+        mbar_arrive_expect_tx(&meta[s].full, tx);
+        if (k > 0) {
+            const size_t off = (size_t)f * sbytes;
+            bulk_load(w, reinterpret_cast<const char *>(a.w_state) + off, sbytes, &meta[s].full);
+            bulk_load(w + a.code.Ep, reinterpret_cast<const char *>(a.l_state) + off, sbytes, &meta[s].full);
+        }
+        if (lbytes)
+            bulk_load(reinterpret_cast<char *>(w) + a.ring_llr_off, a.llr + (size_t)f * a.code.n, lbytes,
+                      &meta[s].full);
     } else {
         mbar_arrive(&meta[s].full);
     }
@@ -1126,6 +1154,8 @@ __global__ void __launch_bounds__(MAXT, 1) decode_kernel_ring(const DecodeArgs a
         if (f < 0) break;  // no more frames
         sm.w = ring_slot<S>(a, smem_raw, s);
         sm.l = sm.w + a.code.Ep;
+        sm.llr = a.ring_llr_off ? reinterpret_cast<const float *>(reinterpret_cast<const char *>(sm.w) + a.ring_llr_off)
+                                : nullptr;
         const FrameIO io = frame_io<S>(a, f);
         frame_run<D, L, DV, S, true>(cv, a.cfg, a.iters_this_launch, io, sm, t, T, bar, unused_phase);
         if (t == 0) {

@@ -49,6 +49,7 @@ struct LaunchCfg {
     // ring kernel (STREAMED): slots, slot size and the offsets of the slots,
     // the groups' scratch and the slot metadata; ring_slots = 0 otherwise
     int ring_slots = 0, ring_slot_bytes = 0, ring_off_slots = 0, ring_off_scratch = 0, ring_off_meta = 0;
+    int ring_llr_off = 0;  // byte offset of the LLR row within a slot, 0 when the slots hold none
 };
 
 // Per-class entry points, defined in lpdec_kD.cu.

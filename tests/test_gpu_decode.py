@@ -165,6 +165,8 @@ def _shape(name):
         return I.socket_code(1024, 4, [16] * 256, 9, name="S16V4")
     if name == "R20":  # checks of degree 10..20, variable degrees 1..4 -> generic wide form
         return I.random_code(600, 60, 10, 20, 8, name="R20")
+    if name == "O601":  # n = 601: LLR rows not a whole number of 16-byte units; checks of degree 4..8
+        return I.random_code(601, 120, 4, 8, 21, name="O601")
     return I.benchmark_code(name, 0)
 
 
@@ -265,6 +267,7 @@ RING_CASES = [
     ("S16V4", "f32", 0.0, 13, [(2, 3)]),
     ("R20", "f32", 1e-5, 17, [(3, 5)]),
     ("C8000", "f16", 1e-5, 7, [(1, 2)]),
+    ("O601", "f32", 1e-5, 23, [(3, 5)]),  # the slots hold no LLR rows (4n not a multiple of 16)
 ]
 
 
@@ -284,7 +287,7 @@ def test_ring_equals_resident(gpu, name, state, eps, frames, rings):
     d_llr = torch.from_numpy(llr).cuda()
     C = gpu.Code(code)
     try:
-        T = {"C1056": 64, "C4000": 256, "S12": 128, "S16V4": 256, "R20": 128, "C8000": 512}[name]
+        T = {"C1056": 64, "C4000": 256, "S12": 128, "S16V4": 256, "R20": 128, "C8000": 512, "O601": 128}[name]
         gpu.lpdec_set_tile(C.handle, dt, T, 1)
         pr = gpu.make_params(eps=eps, max_iter=50, state=state, schedule="resident")
         a = {k: v.cpu().numpy() for k, v in gpu.decode(C, d_llr, pr).items()}
@@ -298,6 +301,34 @@ def test_ring_equals_resident(gpu, name, state, eps, frames, rings):
                 b = {k: v.cpu().numpy() for k, v in gpu.decode(C, d_llr, ps).items()}
                 for k in a:
                     assert np.array_equal(a[k], b[k]), (g, r, ipl, k)
+    finally:
+        C.close()
+
+
+def test_ring_unaligned_llr_batch(gpu, c1056):
+    """An LLR batch that does not start on a 16-byte boundary cannot be copied
+    in bulk: the ring kernel then reads the LLRs from global memory, with the
+    same results."""
+    import torch
+
+    llr = I.awgn_llr(c1056, 2.0, 30, 909)
+    C = gpu.Code(c1056)
+    try:
+        flat = torch.empty(llr.size + 1, dtype=torch.float32, device="cuda")
+        off = flat[1:].view(llr.shape)
+        off.copy_(torch.from_numpy(llr))
+        assert off.data_ptr() % 16 != 0
+        d_llr = torch.from_numpy(llr).cuda()
+        gpu.lpdec_set_tile(C.handle, 0, 64, 1)
+        gpu.lpdec_set_streamed_tile(C.handle, 0, 64, 4, 6)
+        pr = gpu.make_params(eps=1e-5, max_iter=60, schedule="resident")
+        a = {k: v.cpu().numpy() for k, v in gpu.decode(C, d_llr, pr).items()}
+        for ipl in (1, 7):
+            ps = gpu.make_params(eps=1e-5, max_iter=60, schedule="streamed", iters_per_launch=ipl)
+            for src in (d_llr, off):
+                b = {k: v.cpu().numpy() for k, v in gpu.decode(C, src, ps).items()}
+                for k in a:
+                    assert np.array_equal(a[k], b[k]), (ipl, k, src.data_ptr() % 16)
     finally:
         C.close()
 
