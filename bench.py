@@ -118,6 +118,12 @@ def algorithmic_bytes_per_frame_iter(code, state_bytes: int) -> int:
     return 2 * code.E * (2 * state_bytes) + 12 * code.n
 
 
+def moved_bytes_per_frame_iter(code, state_bytes: int) -> int:
+    """2E(s_z + s_lambda) + 4N: what a STREAMED launch of the fused kernel must
+    move per frame-iteration (x never leaves shared memory)."""
+    return 2 * code.E * (2 * state_bytes) + 4 * code.n
+
+
 def _batcher_comparators(n: int) -> int:
     """Comparators of Batcher's odd-even merge sort on n inputs (padded network,
     comparators touching padding dropped): the sort of Algorithm 2's first step."""
@@ -159,10 +165,11 @@ def algorithmic_ops_per_frame_iter(code) -> int:
 KERNEL_SOURCES = ("lpdec_device.cuh", "lpdec_kclass.cuh", "lpdec_internal.h")
 MEASURED_TRAFFIC = {
     # "code/schedule": (source hash, bytes per frame per launch, capture)
-    "C1056/resident": ("ce2c00130157f322", (33_861_376 + 1_797_120) / 8000,
+    "C1056/resident": ("aa97be960672a2c9", (33_889_024 + 1_972_224) / 8000,
                  "profiles/decode_kernel_resident_C1056_small.md: 8000 frames x 300 iterations in one launch (tile 128 x 2)"),
-    "C1056/streamed": ("ce2c00130157f322", (236_644_608 + 141_235_712) / 8000,
-                 "profiles/decode_kernel_streamed_C1056_small.md: one iteration of 8000 frames per launch (tile 128 x 2)"),
+    "C1056/streamed": ("aa97be960672a2c9", (236_646_912 + 141_372_672) / 8000,
+                 "profiles/decode_kernel_ring_streamed_C1056_small.md: one iteration of 8000 frames per launch "
+                 "(ring kernel, tile 192 x 5, 6 slots)"),
 }
 
 
@@ -853,6 +860,11 @@ def main():
     hbm_peak, peak_kind = measured_peaks()
     achieved = bytes_per_launch / (launch_ms / 1000.0) / 1e9
     kname = f"lpdec::decode_kernel ({code.name}, {args.state}, {args.schedule})"
+    if args.schedule == "streamed":
+        ring = lpdec.lpdec_get_tile(C.handle, {"f32": 0, "bf16": 1, "f16": 2}[args.state],
+                                    lpdec.SCHED_STREAMED)["ring_slots"]
+        if ring:
+            kname = f"lpdec::decode_kernel_ring ({code.name}, {args.state}, streamed, {ring} slots)"
     if args.schedule in ("resident", "auto"):
         # State stays in shared memory for all 300 iterations: the kernel is bound
         # by instruction issue, not HBM.  Peak: 152 SMs x 128 FP32 lanes x the
@@ -872,11 +884,16 @@ def main():
                                       "bandwidth; an effective figure, since z/lambda/x never leave the SM"},
         }
     else:
+        Bm = moved_bytes_per_frame_iter(code, state_bytes)
+        moved = F * (ITERS // launches_per_step) * Bm / (launch_ms / 1000.0) / 1e9
         roofline = {
             "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
             "frac": round(achieved / hbm_peak, 4), "traffic": traffic_per_launch(f"{code.name}/streamed", F), "kernel": kname,
             "note": f"peak is the {peak_kind} HBM copy bandwidth; algorithmic bytes {B} per frame-iteration "
-                    f"x {F} frames x {ITERS // launches_per_step} iterations per launch",
+                    f"x {F} frames x {ITERS // launches_per_step} iterations per launch (they count x written and "
+                    f"read once, 8N bytes, which the fused kernel keeps in shared memory, so frac can exceed 1)",
+            "moved": {"bytes_per_frame_iter": Bm, "achieved": round(moved, 1), "frac": round(moved / hbm_peak, 4),
+                      "note": "2E(s_z + s_lambda) + 4N: the bytes a launch must move (state in and out, LLRs in)"},
         }
 
     wer = {}
@@ -918,6 +935,10 @@ def main():
             var[f"{sch}-{st}"] = {"value": F * code.k_design / (vms / 1000.0), "ms_per_step": vms,
                                   "hbm_frac": round(vach / hbm_peak, 4), "launches_per_step": vl,
                                   "tile": vtile}
+            if sch == "streamed":
+                vm = moved_bytes_per_frame_iter(code, 4 if st == "f32" else 2)
+                var[f"{sch}-{st}"]["moved_frac"] = round(
+                    F * (ITERS // vl) * vm / ((vms / vl) / 1000.0) / 1e9 / hbm_peak, 4)
         line["variants"] = var
 
     if not args.no_latency and ws == 1:

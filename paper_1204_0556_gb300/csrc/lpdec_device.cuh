@@ -347,8 +347,9 @@ __device__ __forceinline__ void check_update(const CodeView &c, const IterCfg &p
             const float2 w2 = ld2<S>(ws + e0 + k);  // u = rho x + (1 - rho) w when folded
             const float2 l2 = ld2<S>(ls + e0 + k);
             if constexpr (!RES && kFoldX<S>) {  // regular form (kPairs): ws holds u
-                v[k] = fmaf(p.tmr, l2.x, w2.x);
-                v[k + 1] = fmaf(p.tmr, l2.y, w2.y);
+                const float2 vv = __ffma2_rn(make_float2(p.tmr, p.tmr), l2, w2);  // packed pair, lane = fmaf
+                v[k] = vv.x;
+                v[k + 1] = vv.y;
                 continue;
             }
             const uint32_t cc = ci[k / 2];
@@ -388,9 +389,14 @@ __device__ __forceinline__ void check_update(const CodeView &c, const IterCfg &p
 #pragma unroll
         for (int k = 0; k < D; k += 2) {
             const float z0 = proj_z(v[k], pr, k), z1 = proj_z(v[k + 1], pr, k + 1);
-            const float l0 = v[k] - z0, l1 = v[k + 1] - z1;  // lambda/mu = v - z
-            st2<S>(ls + e0 + k, l0, l1);
-            st2<S>(ws + e0 + k, z0 - l0, z1 - l1);
+            // lambda/mu = v - z and w = z - lambda/mu as packed FP32 pairs (a
+            // product with -1 is exact, so each lane rounds as the subtraction)
+            const float2 m1 = make_float2(-1.0f, -1.0f);
+            const float2 zz = make_float2(z0, z1);
+            const float2 ll = __ffma2_rn(zz, m1, make_float2(v[k], v[k + 1]));
+            const float2 ww = __ffma2_rn(ll, m1, zz);
+            st2<S>(ls + e0 + k, ll.x, ll.y);
+            st2<S>(ws + e0 + k, ww.x, ww.y);
             if constexpr (RES) {
                 float a = xv[k] - z0, b = z0 - zo[k];
                 rp = fmaf(a, a, rp);
@@ -797,7 +803,13 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
                 if (fold) {
                     const float rx = p.rho * x;
 #pragma unroll
-                    for (int s = 0; s < DV; ++s) sm.w[es[s]] = st<S>(fmaf(p.omr, wv[s], rx));
+                    for (int s = 0; s + 1 < DV; s += 2) {  // packed FP32 pairs (each lane rounds as fmaf)
+                        const float2 uu = __ffma2_rn(make_float2(p.omr, p.omr), make_float2(wv[s], wv[s + 1]),
+                                                     make_float2(rx, rx));
+                        sm.w[es[s]] = st<S>(uu.x);
+                        sm.w[es[s + 1]] = st<S>(uu.y);
+                    }
+                    if (DV & 1) sm.w[es[DV - 1]] = st<S>(fmaf(p.omr, wv[DV - 1], rx));
                 }
             } else {
                 const int s0 = __ldg(c.col_ptr + i), s1 = __ldg(c.col_ptr + i + 1);
