@@ -189,14 +189,27 @@ __device__ __forceinline__ Proj project_pp(const float (&v)[D], int d) {
     unsigned th = 0u;
     int key = 0x7fffffff;
     float sdist = 0.0f;
+    // zh_k > 1/2 exactly when v_k > 1/2; tz = zh - 1/2 in packed FP32 pairs
+    // (each lane rounds as the scalar subtraction); |tz| is taken in the sum
+    // and, as the cleared sign bit, in the key.
+    float tz[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-        const float zh = __saturatef(v[k]);
-        if (zh > 0.5f) th |= 1u << k;
-        const float dist = fabsf(zh - 0.5f);
+        if (v[k] > 0.5f) th |= 1u << k;
+        tz[k] = __saturatef(v[k]);
+    }
+#pragma unroll
+    for (int k = 0; k + 1 < D; k += 2) {
+        const float2 t2 = __fadd2_rn(make_float2(tz[k], tz[k + 1]), make_float2(-0.5f, -0.5f));
+        tz[k] = t2.x;
+        tz[k + 1] = t2.y;
+    }
+    if (D & 1) tz[D - 1] = tz[D - 1] - 0.5f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
         if (k < d) {
-            sdist += dist;
-            key = min(key, (__float_as_int(dist) & ~kIdxMask) | k);
+            sdist += fabsf(tz[k]);
+            key = min(key, (__float_as_int(tz[k]) & (0x7fffffff & ~kIdxMask)) | k);
         }
     }
     if ((__popc(th) & 1) == 0) {
@@ -508,15 +521,26 @@ __device__ __forceinline__ void check_update_seg(const CodeView &c, const IterCf
     unsigned th = 0u;
     int key = 0x7fffffff;
     float sdist = 0.0f;
+    // as in project_pp: v > 1/2 for the set, zh - 1/2 in packed pairs, |.| in the sum and key
+    float tz[V];
 #pragma unroll
     for (int k = 0; k < V; ++k) {
-        const float zh = __saturatef(v[k]);
-        if (zh > 0.5f) th |= 1u << k;
-        const float dist = fabsf(zh - 0.5f);
+        if (v[k] > 0.5f) th |= 1u << k;
+        tz[k] = __saturatef(v[k]);
+    }
+#pragma unroll
+    for (int k = 0; k + 1 < V; k += 2) {
+        const float2 t2 = __fadd2_rn(make_float2(tz[k], tz[k + 1]), make_float2(-0.5f, -0.5f));
+        tz[k] = t2.x;
+        tz[k + 1] = t2.y;
+    }
+    if (V & 1) tz[V - 1] = tz[V - 1] - 0.5f;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
         const int q = k * L + r;
         if (q < d) {
-            sdist += dist;
-            key = min(key, (__float_as_int(dist) & ~31) | q);
+            sdist += fabsf(tz[k]);
+            key = min(key, (__float_as_int(tz[k]) & 0x7fffffe0) | q);
         }
     }
     key = seg_min_i<L>(key);
@@ -570,21 +594,37 @@ __device__ __forceinline__ void check_update_seg(const CodeView &c, const IterCf
     Proj pr;
     pr.facet = th;
     pr.beta = beta;
+    // z, then lambda/mu = v - z and w = z - lambda/mu in packed FP32 pairs (each
+    // lane rounds as the subtraction: the product with -1 is exact)
+    float zq[V], lq[V], wq[V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) zq[k] = proj_z(v[k], pr, k);
+#pragma unroll
+    for (int k = 0; k < V; k += 2) {
+        if (k + 1 < V) {
+            const float2 m1 = make_float2(-1.0f, -1.0f), z2 = make_float2(zq[k], zq[k + 1]);
+            const float2 l2 = __ffma2_rn(z2, m1, make_float2(v[k], v[k + 1]));
+            const float2 w2 = __ffma2_rn(l2, m1, z2);
+            lq[k] = l2.x; lq[k + 1] = l2.y; wq[k] = w2.x; wq[k + 1] = w2.y;
+        } else {
+            lq[k] = v[k] - zq[k];
+            wq[k] = zq[k] - lq[k];
+        }
+    }
 #pragma unroll
     for (int k = 0; k < V; ++k) {
         const int q = k * L + r;
         if (q < d) {
             const int e = e0 + q;
-            const float z = proj_z(v[k], pr, k);
+            const float z = zq[k];
             if (need_res) {
                 const float a = xs[col_of(e)] - z;
                 const float b = z - (ld<S>(ws[e]) + ld<S>(ls[e]));
                 rp = fmaf(a, a, rp);
                 rd = fmaf(b, b, rd);
             }
-            const float l = v[k] - z;
-            ls[e] = st<S>(l);
-            ws[e] = st<S>(z - l);
+            ls[e] = st<S>(lq[k]);
+            ws[e] = st<S>(wq[k]);
         }
     }
 }
