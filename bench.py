@@ -915,7 +915,8 @@ def main():
                    "parallelism": f"frames sharded over {ws} rank(s), no collective on the data path"},
         "frames_per_s": ws * F / (ms / 1000.0),
         "wer": wer, "certified_frac": float(cert_h.mean()),
-        "gpu_launches": launches_per_step * args.steps,
+        # STREAMED: one decode launch per iteration plus the check for unfinished frames
+        "gpu_launches": (launches_per_step + (0 if launches_per_step == 1 else 1)) * args.steps,
         "clocks": clocks,
         "roofline": roofline,
     }

@@ -56,6 +56,12 @@ extern "C" {
  * that frame is not decoded (x = 0, bits = 0, cert = 0). */
 #define LPDEC_FRAME_BAD_LLR (-1)
 
+/* Per-frame iteration count written for a STREAMED frame abandoned because a
+ * bounded wait on the movement of its parked state ran out (about 1 s), or
+ * left unfinished after the last launch for that reason: its x, bits and
+ * cert are not valid (cert = 0).  Not expected in normal operation. */
+#define LPDEC_FRAME_ABANDONED (-2)
+
 /* ---- storage type of the per-edge state --------------------------------- */
 /* (The kernels keep w = z - lambda/mu and lambda/mu per edge; Algorithm 1's z
  * is w + lambda/mu.) */
@@ -185,7 +191,8 @@ LPDEC_API int lpdec_get_tile(const lpdec_code *code, int32_t state_dtype, int32_
  *   bits_out:  device pointer, [n_frames x n] uint8: b_i = [x_i > 1/2] (Section 5.1 rounding).
  *   iters_out: device pointer, [n_frames] int32: completed iterations when the stopping
  *              test first passed, or max_iter; LPDEC_FRAME_BAD_LLR for a frame with a
- *              non-finite LLR.
+ *              non-finite LLR; LPDEC_FRAME_ABANDONED (STREAMED) for a frame whose
+ *              state could not be moved in time.
  *   cert_out:  device pointer, [n_frames] uint8: 1 when the output is certified an ML
  *              codeword (Section 1: an integral LP optimum is the ML codeword):
  *              the residual test passes at the final iterate with tolerance

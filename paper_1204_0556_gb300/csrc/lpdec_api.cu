@@ -559,6 +559,17 @@ CodeView make_view(const lpdec_code *c) {
     return v;
 }
 
+// After the last STREAMED launch every frame has k_state = -1; a frame that a
+// stopped group or producer left behind is marked abandoned, so that its stale
+// outputs are never taken for results.
+__global__ void mark_unfinished(int n, const int32_t *__restrict__ k_state, int32_t *iters_out, uint8_t *cert_out) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f < n && k_state[f] >= 0) {
+        if (iters_out) iters_out[f] = kFrameTimeout;
+        if (cert_out) cert_out[f] = 0;
+    }
+}
+
 // Enqueue the decode of n_frames frames.  `work` must hold workspace_bytes().
 size_t workspace_bytes(const lpdec_code *c, int n_frames, int schedule, int dtype, int max_iter, int ipl) {
     size_t b = 256;  // queue counters for the launches, padded
@@ -618,6 +629,11 @@ int enqueue_decode(const lpdec_code *c, int n_frames, const float *llr, const lp
         a.queue = queues + L_;
         err = class_launch(c, p->state_dtype, a, lc);
         if (err != cudaSuccess) return cuda_error(err, "decode kernel launch");
+    }
+    if (schedule == LPDEC_SCHED_STREAMED && n_frames > 0) {
+        mark_unfinished<<<(n_frames + 255) / 256, 256, 0, stream>>>(n_frames, a.k_state, iters_out, cert_out);
+        err = cudaGetLastError();
+        if (err != cudaSuccess) return cuda_error(err, "mark_unfinished launch");
     }
     if (launches_out) *launches_out = launches;
     return LPDEC_OK;

@@ -683,19 +683,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Load of shared data that no thread writes while it is read (a staged LLR
-// row): free to be reordered around shared-memory stores.
-__device__ __forceinline__ float ld_shared_ro(const float *p) {
-    float v;
-    asm("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(smem_addr(p)));
-    return v;
-}
 // LLR i of the frame: from its row copied into shared memory (ring kernel,
-// gs != null), else a read-only global load.
+// gs != null; an ordinary load, so it stays after the wait for the copy),
+// else a read-only global load.
 template <bool READY>
 __device__ __forceinline__ float llr_at(const float *g, const float *gs, int i) {
     if constexpr (READY)
-        if (gs) return ld_shared_ro(gs + i);
+        if (gs) return gs[i];
     return __ldg(g + i);
 }
 
@@ -729,7 +723,7 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 // barrier, the group's) before later async-proxy accesses.
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-constexpr int kFrameTimeout = -2;  // iters_out value of a frame abandoned after a copy timed out
+constexpr int kFrameTimeout = -2;  // iters_out value of a frame abandoned after a copy timed out (LPDEC_FRAME_ABANDONED)
 
 // Decode frame f (RESIDENT) or advance it by up to iters_this_launch
 // iterations (STREAMED), with one group of T threads; t is the thread's rank.
@@ -1048,6 +1042,15 @@ struct RingMeta {
     int pad[2];
 };
 
+// Wait (bounded like mbar_wait_bounded) until a slot's tag holds `seq`.
+__device__ __forceinline__ bool ring_wait_tag(const int *tag, int seq) {
+    const long long start = clock64();
+    while (*reinterpret_cast<const volatile int *>(tag) != seq) {
+        if (clock64() - start > (1ll << 31)) return false;
+    }
+    return true;
+}
+
 template <typename S>
 __device__ __forceinline__ S *ring_slot(const DecodeArgs &a, unsigned char *smem_raw, int s) {
     return reinterpret_cast<S *>(smem_raw + a.ring_off_slots + (size_t)s * a.ring_slot_bytes);
@@ -1071,7 +1074,7 @@ __device__ __forceinline__ bool ring_publish(const DecodeArgs &a, unsigned char 
     }
     if (*abort_flag) return false;
     meta[s].frame = f;
-    meta[s].seq = seq;
+    *reinterpret_cast<volatile int *>(&meta[s].seq) = seq;  // the tag groups wait for (ring_wait_tag)
     const uint32_t sbytes = (uint32_t)((size_t)a.code.Ep * sizeof(S));
     const uint32_t lbytes = a.ring_llr_off ? (uint32_t)a.code.n * 4u : 0u;  // a multiple of 16 (host checks)
     const uint32_t tx = f < 0 ? 0u : (k > 0 ? 2u * sbytes : 0u) + lbytes;
@@ -1186,7 +1189,14 @@ __global__ void __launch_bounds__(MAXT, 1) decode_kernel_ring(const DecodeArgs a
         par ^= 1;
         const int s = my % R;
         const uint32_t ph = (uint32_t)(my / R) & 1u;
-        if (t == 0) sm.flags[3] = mbar_wait_bounded(&meta[s].full, ph) ? 1 : 0;
+        // A parity wait cannot tell this round from the round two before it.
+        // Copies land out of order, so when this group claims `my` the slot may
+        // still be in its previous round (my - R published, copies in flight),
+        // or already past this one.  So first wait until the slot's tag reads
+        // `my`: the producer writes it before publishing, and publishes `my`
+        // only after my - R was released, so the slot is then in this round or
+        // just past it, which the parity wait tells apart.
+        if (t == 0) sm.flags[3] = (ring_wait_tag(&meta[s].seq, my) && mbar_wait_bounded(&meta[s].full, ph)) ? 1 : 0;
         group_sync(bar, T);
         if (sm.flags[3] == 0) {
             if (t == 0) {

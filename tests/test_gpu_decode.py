@@ -305,6 +305,43 @@ def test_ring_equals_resident(gpu, name, state, eps, frames, rings):
         C.close()
 
 
+@pytest.mark.parametrize("state,groups", [("f32", 5), ("bf16", 9)])
+def test_ring_many_frames_every_frame_finishes(gpu, c1056, state, groups):
+    """Many frames through a ring with one spare slot (R = G + 1), where the
+    copies of consecutive frames complete out of order most often: every frame
+    finishes (no LPDEC_FRAME_ABANDONED, no output left unwritten: the output
+    buffers start out holding sentinels) and equals the RESIDENT decode."""
+    import torch
+
+    F, iters = 12000, 40
+    llr = I.awgn_llr(c1056, 2.0, F, 1212)
+    d_llr = torch.from_numpy(llr).cuda()
+    dt = {"f32": 0, "bf16": 1}[state]
+    T = 96
+    C = gpu.Code(c1056)
+    try:
+        gpu.lpdec_set_tile(C.handle, dt, T, 1)
+        gpu.lpdec_set_streamed_tile(C.handle, dt, T, groups, groups + 1)
+
+        def run(schedule):
+            out = {"x": torch.full((F, c1056.n), float("nan"), device="cuda"),
+                   "bits": torch.full((F, c1056.n), 7, dtype=torch.uint8, device="cuda"),
+                   "iters": torch.full((F,), -7, dtype=torch.int32, device="cuda"),
+                   "cert": torch.full((F,), 7, dtype=torch.uint8, device="cuda")}
+            p = gpu.make_params(eps=0.0, max_iter=iters, state=state, schedule=schedule)
+            gpu.decode(C, d_llr, p, out=out)
+            return {k: v.cpu().numpy() for k, v in out.items()}
+
+        a = run("resident")
+        for _ in range(2):
+            b = run("streamed")
+            assert np.all(b["iters"] == iters)
+            for k in a:
+                assert np.array_equal(a[k], b[k]), k
+    finally:
+        C.close()
+
+
 def test_ring_unaligned_llr_batch(gpu, c1056):
     """An LLR batch that does not start on a 16-byte boundary cannot be copied
     in bulk: the ring kernel then reads the LLRs from global memory, with the
