@@ -215,6 +215,11 @@ LPDEC_API int lpdec_decode(const lpdec_code *code, int32_t n_frames, const float
  * As lpdec_decode, but every buffer is a HOST pointer: the call copies llr to
  * the device, decodes, copies the outputs back and synchronizes the stream
  * before returning.  Outputs have the same meaning and shapes as above.
+ * A batch of at least 8 waves (a wave: the frames the kernel holds in flight)
+ * is cut into up to 8 chunks of whole waves, decoded alternately on
+ * cuda_stream and an internal second stream so that the copies of one chunk
+ * overlap the decode of its neighbours (results unchanged).  Page-locked host
+ * buffers are needed for that overlap.
  */
 LPDEC_API int lpdec_decode_host(const lpdec_code *code, int32_t n_frames, const float *llr,
                       const lpdec_params *params, float *x_out, uint8_t *bits_out,
@@ -352,6 +357,16 @@ LPDEC_API int lpdec_server_destroy(lpdec_server *server);
  * Errors: LPDEC_EINVAL for d outside [1, 32], count < 0 or NULL pointers.
  */
 LPDEC_API int lpdec_project(int32_t d, int64_t count, const float *v, float *z, void *cuda_stream);
+
+/*
+ * Device memory.  The decode calls allocate their device workspace and (host
+ * entry points) buffers stream-ordered from one memory pool per device owned
+ * by the library, which keeps freed memory for later calls instead of
+ * returning it at each synchronization.  This call returns every pool's
+ * unused memory to the driver; memory of calls still in flight stays.
+ * Errors: LPDEC_ECUDA if a pool cannot be trimmed.
+ */
+LPDEC_API int lpdec_release_memory(void);
 
 /* ---- dual subgradient decoding (appendix) ------------------------------- */
 

@@ -278,6 +278,43 @@ extern "C" int lpdec_code_destroy(lpdec_code *c) {
 // launch plumbing
 namespace lpdec {
 
+// Stream-ordered allocations of the library come from one memory pool per
+// device that keeps freed memory for the next call (no release threshold):
+// a call that synchronizes then does not hand its buffers back to the driver
+// and map them again on the next call.  lpdec_release_memory trims the pools.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64];
+
+cudaError_t lib_alloc(void **ptr, size_t bytes, cudaStream_t stream) {
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    if (dev < 0 || dev >= 64) return cudaMallocAsync(ptr, bytes, stream);
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        if (!g_pool[dev]) {
+            cudaMemPoolProps props;
+            std::memset(&props, 0, sizeof(props));
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            cudaMemPool_t p = nullptr;
+            err = cudaMemPoolCreate(&p, &props);
+            if (err != cudaSuccess) return err;
+            uint64_t keep = ~0ull;
+            err = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+            if (err != cudaSuccess) {
+                cudaMemPoolDestroy(p);
+                return err;
+            }
+            g_pool[dev] = p;
+        }
+        pool = g_pool[dev];
+    }
+    return cudaMallocFromPoolAsync(ptr, bytes, pool, stream);
+}
+
 static cudaError_t class_prepare(const lpdec_code *c, int dtype, bool stage, bool ring, size_t smem) {
     switch (kClassD[c->cls]) {
         case 6: return prepare_decode_6(dtype, c->reg_dv, stage, ring, smem);
@@ -673,8 +710,8 @@ extern "C" int lpdec_decode(const lpdec_code *c, int32_t n_frames, const float *
     const int schedule = lpdec::resolve_schedule(c, p, tile);
     const size_t wb = lpdec::workspace_bytes(c, n_frames, schedule, p->state_dtype, p->max_iter, p->iters_per_launch);
     void *work = nullptr;
-    cudaError_t err = cudaMallocAsync(&work, wb, stream);
-    if (err != cudaSuccess) return cuda_error(err, "lpdec_decode: cudaMallocAsync of the workspace");
+    cudaError_t err = lpdec::lib_alloc(&work, wb, stream);
+    if (err != cudaSuccess) return cuda_error(err, "lpdec_decode: allocation of the workspace");
     rc = lpdec::enqueue_decode(c, n_frames, llr, p, x_out, bits_out, iters_out, cert_out, stream, work, schedule,
                                tile, nullptr);
     err = cudaFreeAsync(work, stream);
@@ -682,6 +719,20 @@ extern "C" int lpdec_decode(const lpdec_code *c, int32_t n_frames, const float *
     if (err != cudaSuccess) return cuda_error(err, "lpdec_decode: cudaFreeAsync");
     return LPDEC_OK;
 }
+
+namespace {
+// Frames the decode kernel holds in flight at once for this batch (CTAs x
+// groups), or 0 if the launch cannot be planned.
+int frames_in_flight(const lpdec_code *c, const lpdec_params *p, int n_frames, cudaStream_t stream) {
+    lpdec::Tile tile = lpdec::chosen_tile(c, p);
+    const int schedule = lpdec::resolve_schedule(c, p, tile);
+    if (schedule != LPDEC_SCHED_STREAMED) tile.ring = 0;
+    lpdec::LaunchCfg lc;
+    lpdec::SliceLayout L;
+    if (lpdec::plan_launch(c, p->state_dtype, tile, n_frames, stream, &lc, &L)) return 0;
+    return lc.grid * tile.groups;
+}
+}  // namespace
 
 extern "C" int lpdec_decode_host(const lpdec_code *c, int32_t n_frames, const float *llr, const lpdec_params *p,
                                  float *x_out, uint8_t *bits_out, int32_t *iters_out, uint8_t *cert_out,
@@ -693,33 +744,79 @@ extern "C" int lpdec_decode_host(const lpdec_code *c, int32_t n_frames, const fl
     if (n_frames == 0) return LPDEC_OK;
     if (!llr || !x_out) return set_error(LPDEC_EINVAL, "lpdec_decode_host: llr and x_out must not be NULL");
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
-    const size_t nx = (size_t)n_frames * c->n;
-    const size_t bytes = nx * 4 /*llr*/ + nx * 4 /*x*/ + nx /*bits*/ + (size_t)n_frames * 5 + 4 * 256;
-    char *buf = nullptr;
-    cudaError_t err = cudaMallocAsync(reinterpret_cast<void **>(&buf), bytes, stream);
-    if (err != cudaSuccess) return cuda_error(err, "lpdec_decode_host: cudaMallocAsync");
+    const size_t n = (size_t)c->n;
+    const size_t nx = (size_t)n_frames * n;
     auto align = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    const size_t bytes = align(nx * 4) * 2 + align(nx) + align((size_t)n_frames * 4) + align((size_t)n_frames);
+    char *buf = nullptr;
+    cudaError_t err = lpdec::lib_alloc(reinterpret_cast<void **>(&buf), bytes, stream);
+    if (err != cudaSuccess) return cuda_error(err, "lpdec_decode_host: allocation of device buffers");
     float *d_llr = reinterpret_cast<float *>(buf);
     float *d_x = reinterpret_cast<float *>(buf + align(nx * 4));
-    uint8_t *d_bits = reinterpret_cast<uint8_t *>(buf + align(nx * 4) + align(nx * 4));
+    uint8_t *d_bits = reinterpret_cast<uint8_t *>(buf + align(nx * 4) * 2);
     int32_t *d_iters = reinterpret_cast<int32_t *>(buf + align(nx * 4) * 2 + align(nx));
     uint8_t *d_cert = reinterpret_cast<uint8_t *>(buf + align(nx * 4) * 2 + align(nx) + align((size_t)n_frames * 4));
-    rc = LPDEC_OK;
-    err = cudaMemcpyAsync(d_llr, llr, nx * 4, cudaMemcpyHostToDevice, stream);
-    if (err != cudaSuccess) rc = cuda_error(err, "lpdec_decode_host: copy of llr");
-    if (!rc) rc = lpdec_decode(c, n_frames, d_llr, p, d_x, bits_out ? d_bits : nullptr, iters_out ? d_iters : nullptr,
-                               cert_out ? d_cert : nullptr, cuda_stream);
-    if (!rc) {
-        err = cudaMemcpyAsync(x_out, d_x, nx * 4, cudaMemcpyDeviceToHost, stream);
-        if (err == cudaSuccess && bits_out) err = cudaMemcpyAsync(bits_out, d_bits, nx, cudaMemcpyDeviceToHost, stream);
+
+    // Pipelining: a large batch is cut into chunks of whole waves (the frames the
+    // kernel holds in flight), decoded alternately on the caller's stream and a
+    // second stream, so that each chunk's LLR copy overlaps the previous chunk's
+    // decode and its output copy the next one's.  The first and last chunks are
+    // one wave each, so that little is copied before the first decode or after
+    // the last.  Each frame's arithmetic does not depend on the batch, so the
+    // results are those of one decode.
+    const int wave = frames_in_flight(c, p, n_frames, stream);
+    std::vector<int> cut{0};  // chunk k holds frames [cut[k], cut[k+1])
+    if (wave > 0 && n_frames >= 8 * wave) {
+        const int waves = (n_frames + wave - 1) / wave;
+        const int mid = waves - 2, k = std::min(6, std::max(1, mid / 4));
+        const int per = (mid + k - 1) / k;
+        cut.push_back(wave);
+        for (int w = 1 + per; w < waves - 1; w += per) cut.push_back(w * wave);
+        cut.push_back((waves - 1) * wave);
+    }
+    cut.push_back(n_frames);
+    int chunks = (int)cut.size() - 1;
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    if (chunks > 1) {
+        err = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+        if (err == cudaSuccess) err = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+        if (err == cudaSuccess) err = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+        if (err == cudaSuccess) err = cudaEventRecord(fork, stream);  // after the allocation
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(side, fork, 0);
+        if (err != cudaSuccess) {
+            rc = cuda_error(err, "lpdec_decode_host: second stream");
+            chunks = 0;
+        }
+    }
+    for (int k = 0; k < chunks && !rc; ++k) {
+        const int f0 = cut[k], nf = cut[k + 1] - cut[k];
+        cudaStream_t s = (k & 1) ? side : stream;
+        const size_t o = (size_t)f0 * n, cnt = (size_t)nf * n;
+        err = cudaMemcpyAsync(d_llr + o, llr + o, cnt * 4, cudaMemcpyHostToDevice, s);
+        if (err != cudaSuccess) { rc = cuda_error(err, "lpdec_decode_host: copy of llr"); break; }
+        rc = lpdec_decode(c, nf, d_llr + o, p, d_x + o, bits_out ? d_bits + o : nullptr,
+                          iters_out ? d_iters + f0 : nullptr, cert_out ? d_cert + f0 : nullptr, s);
+        if (rc) break;
+        err = cudaMemcpyAsync(x_out + o, d_x + o, cnt * 4, cudaMemcpyDeviceToHost, s);
+        if (err == cudaSuccess && bits_out) err = cudaMemcpyAsync(bits_out + o, d_bits + o, cnt, cudaMemcpyDeviceToHost, s);
         if (err == cudaSuccess && iters_out)
-            err = cudaMemcpyAsync(iters_out, d_iters, (size_t)n_frames * 4, cudaMemcpyDeviceToHost, stream);
+            err = cudaMemcpyAsync(iters_out + f0, d_iters + f0, (size_t)nf * 4, cudaMemcpyDeviceToHost, s);
         if (err == cudaSuccess && cert_out)
-            err = cudaMemcpyAsync(cert_out, d_cert, (size_t)n_frames, cudaMemcpyDeviceToHost, stream);
+            err = cudaMemcpyAsync(cert_out + f0, d_cert + f0, (size_t)nf, cudaMemcpyDeviceToHost, s);
         if (err != cudaSuccess) rc = cuda_error(err, "lpdec_decode_host: copy of outputs");
+    }
+    if (side) {  // join the second stream back before the buffer is freed
+        cudaError_t ej = cudaEventRecord(join, side);
+        if (ej == cudaSuccess) ej = cudaStreamWaitEvent(stream, join, 0);
+        if (ej != cudaSuccess) cudaStreamSynchronize(side);
+        if (!rc && ej != cudaSuccess) rc = cuda_error(ej, "lpdec_decode_host: join");
     }
     cudaError_t e2 = cudaFreeAsync(buf, stream);
     cudaError_t e3 = cudaStreamSynchronize(stream);
+    if (side) cudaStreamDestroy(side);
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
     if (rc) return rc;
     if (e2 != cudaSuccess) return cuda_error(e2, "lpdec_decode_host: cudaFreeAsync");
     if (e3 != cudaSuccess) return cuda_error(e3, "lpdec_decode_host: cudaStreamSynchronize");
@@ -783,8 +880,8 @@ extern "C" int lpdec_autotune(lpdec_code *c, const lpdec_params *p, int32_t n_fr
     const size_t nx = (size_t)n_frames * c->n;
     char *buf = nullptr;
     const size_t wb = lpdec::workspace_bytes(c, n_frames, q.schedule, q.state_dtype, q.max_iter, q.iters_per_launch);
-    cudaError_t err = cudaMallocAsync(reinterpret_cast<void **>(&buf), nx * 4 + 256 + wb, stream);
-    if (err != cudaSuccess) return cuda_error(err, "lpdec_autotune: cudaMallocAsync");
+    cudaError_t err = lpdec::lib_alloc(reinterpret_cast<void **>(&buf), nx * 4 + 256 + wb, stream);
+    if (err != cudaSuccess) return cuda_error(err, "lpdec_autotune: allocation of device buffers");
     float *x = reinterpret_cast<float *>(buf);
     void *work = buf + ((nx * 4 + 255) & ~(size_t)255);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -901,6 +998,16 @@ extern "C" int lpdec_get_tile(const lpdec_code *c, int32_t state_dtype, int32_t 
     if (group_threads) *group_threads = t.group_threads;
     if (groups) *groups = t.groups;
     if (ring_slots) *ring_slots = schedule == LPDEC_SCHED_RESIDENT ? 0 : t.ring;
+    return LPDEC_OK;
+}
+
+extern "C" int lpdec_release_memory(void) {
+    std::lock_guard<std::mutex> lk(lpdec::g_pool_mu);
+    for (int d = 0; d < 64; ++d) {
+        if (!lpdec::g_pool[d]) continue;
+        cudaError_t err = cudaMemPoolTrimTo(lpdec::g_pool[d], 0);
+        if (err != cudaSuccess) return cuda_error(err, "lpdec_release_memory: cudaMemPoolTrimTo");
+    }
     return LPDEC_OK;
 }
 

@@ -24,6 +24,9 @@ struct SliceLayout {
 };
 
 int set_error(int code, const char *fmt, ...);
+// Stream-ordered allocation from the library's per-device memory pool (freed
+// with cudaFreeAsync; the pool keeps the memory for later calls).
+cudaError_t lib_alloc(void **ptr, size_t bytes, cudaStream_t stream);
 int cuda_error(cudaError_t e, const char *what);
 int validate_params(const lpdec_params *p);
 IterCfg make_cfg(const lpdec_code *c, const lpdec_params *p);

@@ -402,8 +402,8 @@ extern "C" int lpdec_decode_dual(const lpdec_code *c, int32_t n_frames, const fl
     const int grid = (int)std::max<long long>(1, std::min<long long>(need, (long long)bps * lpdec::device_sm_count(c->device)));
 
     int *queue = nullptr;
-    err = cudaMallocAsync(reinterpret_cast<void **>(&queue), sizeof(int), stream);
-    if (err != cudaSuccess) return cuda_error(err, "lpdec_decode_dual: cudaMallocAsync");
+    err = lpdec::lib_alloc(reinterpret_cast<void **>(&queue), sizeof(int), stream);
+    if (err != cudaSuccess) return cuda_error(err, "lpdec_decode_dual: allocation of the queue");
     err = cudaMemsetAsync(queue, 0, sizeof(int), stream);
     int rc = LPDEC_OK;
     if (err != cudaSuccess) rc = cuda_error(err, "lpdec_decode_dual: cudaMemsetAsync");

@@ -352,8 +352,8 @@ extern "C" int lpdec_decode_mixed(const lpdec_code *const *codes, int32_t n_code
     if (!llr || !x_out) return set_error(LPDEC_EINVAL, "lpdec_decode_mixed: llr and x_out must not be NULL");
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
     char *work = nullptr;
-    cudaError_t err = cudaMallocAsync(reinterpret_cast<void **>(&work), S.work_bytes(), stream);
-    if (err != cudaSuccess) return cuda_error(err, "lpdec_decode_mixed: cudaMallocAsync");
+    cudaError_t err = lib_alloc(reinterpret_cast<void **>(&work), S.work_bytes(), stream);
+    if (err != cudaSuccess) return cuda_error(err, "lpdec_decode_mixed: allocation of the workspace");
     mixed_bind(S, work, llr, x_out, bits_out, iters_out, cert_out);
     err = cudaMemcpyAsync(S.d_offset, S.offset.data(), S.offset.size() * 8, cudaMemcpyHostToDevice, stream);
     if (err == cudaSuccess)

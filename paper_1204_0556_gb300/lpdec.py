@@ -42,6 +42,7 @@ EXPORTED = [
     "lpdec_server_stats", "lpdec_server_destroy", "lpdec_autotune", "lpdec_set_tile", "lpdec_server_counters",
     "lpdec_mixed_plan_create", "lpdec_mixed_plan_decode", "lpdec_mixed_plan_destroy",
     "lpdec_decode_dual", "lpdec_dual_set_tile", "lpdec_set_streamed_tile", "lpdec_get_tile",
+    "lpdec_release_memory",
 ]
 
 
@@ -118,6 +119,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
             "lpdec_dual_set_tile": (ctypes.c_int, [_vp, _i32, _i32]),
             "lpdec_set_streamed_tile": (ctypes.c_int, [_vp, _i32, _i32, _i32, _i32]),
             "lpdec_get_tile": (ctypes.c_int, [_vp, _i32, _i32, _i32p, _i32p, _i32p]),
+            "lpdec_release_memory": (ctypes.c_int, []),
         })
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -260,6 +262,10 @@ def lpdec_set_tile(handle: int, state_dtype: int, group_threads: int, groups: in
 def lpdec_set_streamed_tile(handle: int, state_dtype: int, group_threads: int, groups: int,
                             ring_slots: int = 0) -> None:
     _check(load().lpdec_set_streamed_tile(handle, state_dtype, group_threads, groups, ring_slots))
+
+
+def lpdec_release_memory() -> None:
+    _check(load().lpdec_release_memory())
 
 
 def lpdec_get_tile(handle: int, state_dtype: int, schedule: int) -> dict:

@@ -483,6 +483,39 @@ def test_host_entry_point_matches_device_entry(gpu, c96):
         assert np.array_equal(a[k], b[k]), k
 
 
+@pytest.mark.parametrize("schedule", ["resident", "streamed"])
+def test_host_entry_point_pipelined_chunks(gpu, c1056, schedule):
+    """A host batch of several waves (tile 6 x 160: 912 frames in flight) is
+    decoded in chunks on two streams with the copies overlapped; the results
+    equal one device-side decode of the whole batch."""
+    import torch
+
+    F = 8000
+    llr = I.awgn_llr(c1056, 2.25, F, 1313)
+    C = gpu.Code(c1056)
+    try:
+        gpu.lpdec_set_tile(C.handle, 0, 160, 6)
+        p = gpu.make_params(eps=1e-5, max_iter=40, schedule=schedule)
+        a = {k: v.cpu().numpy() for k, v in gpu.decode(C, torch.from_numpy(llr).cuda(), p).items()}
+        b = gpu.decode_host(C, llr, p)
+        for k in a:
+            assert np.array_equal(a[k], b[k]), k
+    finally:
+        C.close()
+
+
+def test_release_memory_between_decodes(gpu, c96):
+    """The library's memory pool can be trimmed between decodes, and decodes
+    after the trim allocate again and give the same results."""
+    llr = I.awgn_llr(c96, 2.0, 40, 16)
+    a = gpu_decode(gpu, c96, llr, eps=1e-5, max_iter=80)
+    gpu.lpdec_release_memory()
+    b = gpu_decode(gpu, c96, llr, eps=1e-5, max_iter=80, schedule="streamed")
+    gpu.lpdec_release_memory()
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
 def _wilson(k, n, z=1.96):
     p = k / n
     den = 1 + z * z / n
