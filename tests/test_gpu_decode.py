@@ -370,6 +370,30 @@ def test_ring_unaligned_llr_batch(gpu, c1056):
         C.close()
 
 
+def test_ring_single_frame_and_single_iteration(gpu, c1056):
+    """Ring launches with one frame (fewer frames than groups, the other groups
+    take sentinels at once), with one iteration in all, and an empty batch."""
+    import torch
+
+    llr = I.awgn_llr(c1056, 2.0, 3, 1414)
+    C = gpu.Code(c1056)
+    try:
+        gpu.lpdec_set_tile(C.handle, 0, 64, 1)
+        gpu.lpdec_set_streamed_tile(C.handle, 0, 64, 4, 6)
+        for F, iters in [(1, 1), (1, 25), (3, 1)]:
+            d = torch.from_numpy(llr[:F]).cuda()
+            a = {k: v.cpu().numpy() for k, v in
+                 gpu.decode(C, d, gpu.make_params(eps=0.0, max_iter=iters, schedule="resident")).items()}
+            b = {k: v.cpu().numpy() for k, v in
+                 gpu.decode(C, d, gpu.make_params(eps=0.0, max_iter=iters, schedule="streamed")).items()}
+            for k in a:
+                assert np.array_equal(a[k], b[k]), (F, iters, k)
+        gpu.lpdec_decode(C.handle, 0, 0, gpu.make_params(schedule="streamed"), 0, 0, 0, 0,
+                         int(torch.cuda.current_stream().cuda_stream))
+    finally:
+        C.close()
+
+
 def test_ring_tile_validation(gpu, c1056):
     """Ring tiles that cannot run are refused before any launch."""
     C = gpu.Code(c1056)
