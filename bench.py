@@ -165,9 +165,9 @@ def algorithmic_ops_per_frame_iter(code) -> int:
 KERNEL_SOURCES = ("lpdec_device.cuh", "lpdec_kclass.cuh", "lpdec_internal.h")
 MEASURED_TRAFFIC = {
     # "code/schedule": (source hash, bytes per frame per launch, capture)
-    "C1056/resident": ("ec75e0608198066e", (33_858_304 + 1_968_128) / 8000,
+    "C1056/resident": ("fd269eab778905c0", (33_912_064 + 1_916_928) / 8000,
                  "profiles/decode_kernel_resident_C1056_small.md: 8000 frames x 300 iterations in one launch (tile 128 x 2)"),
-    "C1056/streamed": ("ec75e0608198066e", (236_682_496 + 141_109_504) / 8000,
+    "C1056/streamed": ("fd269eab778905c0", (236_647_680 + 141_243_136) / 8000,
                  "profiles/decode_kernel_ring_streamed_C1056_small.md: one iteration of 8000 frames per launch "
                  "(ring kernel, tile 192 x 5, 6 slots)"),
 }
