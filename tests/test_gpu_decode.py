@@ -49,13 +49,16 @@ def syndromes(code, bits):
     return (bits.astype(np.int64) @ H.T) % 2
 
 
-def assert_parity(code, got, ref, xtol, same_iters=True):
+def assert_parity(code, got, ref, xtol, same_iters=True, min_clean=0.5):
+    """x within xtol on every frame; bits, certificates and syndromes identical
+    on the clean frames (no x within 1e-3 of 1/2 or of the certificate bound),
+    which must be more than min_clean of the frames for the check to mean much."""
     if same_iters:
         assert np.array_equal(got["iters"], ref["iters"])
     err = np.abs(got["x"] - ref["x"]).max(axis=1)
     assert err.max() <= xtol, (err.max(), int(np.argmax(err)))
     clean = clean_frames(ref)
-    assert clean.mean() > 0.5
+    assert clean.mean() > min_clean
     assert np.array_equal(got["bits"][clean], ref["bits"][clean])
     assert np.array_equal(got["cert"][clean], ref["cert"][clean])
     s_got, s_ref = syndromes(code, got["bits"]), syndromes(code, ref["bits"])
@@ -109,6 +112,74 @@ def test_c1056_fixed_300(gpu, oracle_mod, c1056, schedule):
     got = gpu_decode(gpu, c1056, llr, schedule=schedule, **kw)
     ref = oracle_decode(oracle_mod, c1056, llr, **kw)
     assert_parity(c1056, got, ref, 1e-4)
+
+
+def test_c1056_full_bench_size(gpu, oracle_mod, c1056):
+    """The bench's workload at full size: 4 x 10^4 frames (10^4 at each of 1.5,
+    2.0, 2.5 and 3.0 dB, LLR seeds 100..103), 300 fixed iterations, in the
+    bench's RESIDENT launch configuration (6 groups of 160 threads per CTA).
+    Sampled frames equal the oracle's decodes of the same frames (frames are
+    decoded independently, so the oracle runs them alone), and the whole batch
+    through the STREAMED ring kernel (one launch per iteration) equals the
+    RESIDENT decode bit for bit, every frame finished."""
+    import torch
+
+    per = 10_000
+    llr = np.concatenate([I.awgn_llr(c1056, snr, per, seed)
+                          for snr, seed in zip((1.5, 2.0, 2.5, 3.0), (100, 101, 102, 103))])
+    F = len(llr)
+    d_llr = torch.from_numpy(llr).cuda()
+    C = gpu.Code(c1056)
+    try:
+        gpu.lpdec_set_tile(C.handle, 0, 160, 6)
+        gpu.lpdec_set_streamed_tile(C.handle, 0, 160, 5, 6)
+
+        def run(schedule):
+            out = {"x": torch.full((F, c1056.n), float("nan"), device="cuda"),
+                   "bits": torch.full((F, c1056.n), 7, dtype=torch.uint8, device="cuda"),
+                   "iters": torch.full((F,), -7, dtype=torch.int32, device="cuda"),
+                   "cert": torch.full((F,), 7, dtype=torch.uint8, device="cuda")}
+            gpu.decode(C, d_llr, gpu.make_params(mu=MU, rho=RHO, eps=0.0, max_iter=300, schedule=schedule), out=out)
+            return {k: v.cpu().numpy() for k, v in out.items()}
+
+        a = run("resident")
+        assert np.all(a["iters"] == 300)
+        rng = np.random.default_rng(17)
+        sample = np.sort(np.concatenate([p * per + rng.choice(per, 6, replace=False) for p in range(4)]))
+        ref = oracle_decode(oracle_mod, c1056, llr[sample], mu=MU, rho=RHO, eps=0.0, max_iter=300)
+        assert_parity(c1056, {k: v[sample] for k, v in a.items()}, ref, 1e-4)
+        b = run("streamed")
+        for k in a:
+            assert np.array_equal(a[k], b[k]), k
+    finally:
+        C.close()
+
+
+@pytest.mark.parametrize("name,seed,tile", [("C4000", 2, (800, 1)), ("C8000", 3, (928, 1))])
+def test_wide_codes_full_bench_size(gpu, oracle_mod, name, seed, tile):
+    """`bench.py --code C4000 | C8000` at full size (4 x 10^4 frames over the four
+    Eb/N0 points, 300 fixed iterations, RESIDENT, the bench's tile): sampled
+    frames equal the oracle's decodes of the same frames.  Many C8000 frames at
+    these Eb/N0 stay fractional near 1/2 (its WER is high), so a quarter of the
+    sample suffices for the bit and certificate comparison."""
+    import torch
+
+    code = I.benchmark_code(name, seed)
+    per = 10_000
+    llr = np.concatenate([I.awgn_llr(code, snr, per, s)
+                          for snr, s in zip((1.5, 2.0, 2.5, 3.0), (100, 101, 102, 103))])
+    C = gpu.Code(code)
+    try:
+        gpu.lpdec_set_tile(C.handle, 0, *tile)
+        out = gpu.decode(C, torch.from_numpy(llr).cuda(),
+                         gpu.make_params(mu=MU, rho=RHO, eps=0.0, max_iter=300, schedule="resident"))
+        got = {k: v.cpu().numpy() for k, v in out.items()}
+    finally:
+        C.close()
+    rng = np.random.default_rng(29)
+    sample = np.sort(np.concatenate([p * per + rng.choice(per, 4, replace=False) for p in range(4)]))
+    ref = oracle_decode(oracle_mod, code, llr[sample], mu=MU, rho=RHO, eps=0.0, max_iter=300)
+    assert_parity(code, {k: v[sample] for k, v in got.items()}, ref, 1e-4, min_clean=0.25)
 
 
 @pytest.mark.parametrize("snr,seed", [(2.5, 202), (1.5, 303)])
