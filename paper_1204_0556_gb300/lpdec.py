@@ -26,6 +26,7 @@ LPDEC_ETIMEOUT = -4
 LPDEC_EBUSY = -5
 LPDEC_ECLOSED = -6
 LPDEC_FRAME_BAD_LLR = -1
+LPDEC_FRAME_ABANDONED = -2
 
 STATE_F32, STATE_BF16, STATE_F16 = 0, 1, 2
 SCHED_AUTO, SCHED_STREAMED, SCHED_RESIDENT = 0, 1, 2

@@ -31,6 +31,20 @@ def _declared_symbols():
     return names
 
 
+def test_header_constants_match_the_binding():
+    """Every integer #define LPDEC_* of the header has the binding's value
+    (status codes, per-frame statuses, state types, schedules)."""
+    txt = open(os.path.join(ROOT, "include", "lpdec.h")).read()
+    defs = dict(re.findall(r"^#define (LPDEC_\w+)\s+\(?(-?\d+)\)?", txt, re.M))
+    assert len(defs) >= 15
+    for name, val in defs.items():
+        if hasattr(L, name):
+            py = getattr(L, name)
+        else:  # LPDEC_STATE_F32 -> STATE_F32, LPDEC_SCHED_AUTO -> SCHED_AUTO
+            py = getattr(L, name[len("LPDEC_"):])
+        assert py == int(val), name
+
+
 def test_every_declared_symbol_is_exported(lib):
     declared = _declared_symbols()
     assert len(declared) >= 9
