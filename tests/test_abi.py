@@ -110,6 +110,19 @@ def test_decode_and_project_reject_bad_arguments(lib):
     assert lib.lpdec_project(6, 0, None, None, None) == L.LPDEC_OK
 
 
+def test_tile_calls_reject_bad_arguments(lib):
+    """Host-side checks of the tile setters and getter (no code object, no GPU)."""
+    gt, g, r = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    assert lib.lpdec_set_streamed_tile(None, 0, 64, 2, 3) == L.LPDEC_EINVAL
+    assert lib.lpdec_get_tile(None, 0, L.SCHED_STREAMED, ctypes.byref(gt), ctypes.byref(g), ctypes.byref(r)) == L.LPDEC_EINVAL
+    assert lib.lpdec_set_tile(None, 0, 64, 2) == L.LPDEC_EINVAL
+
+
+def test_release_memory_without_pools(lib):
+    """With no decode run yet in this process there is no pool to trim."""
+    assert lib.lpdec_release_memory() == L.LPDEC_OK
+
+
 def test_python_binding_fails_loudly_without_library(tmp_path):
     saved = L._lib
     try:
