@@ -15,7 +15,7 @@
  *                          the over-relaxation of Section 5.2.
  *
  * All arithmetic is double precision.  Readings taken where the paper is
- * silent or garbled (each is also listed in the design notes):
+ * silent or garbled:
  *   - Algorithm 2's final else-branch is garbled.  Instead of it, the bracket
  *     [beta_i, beta_{i+1}] of consecutive breakpoints with g(beta_i) > r >=
  *     g(beta_{i+1}) is located on the FULL breakpoint set E1, L1, E2, L2, 0 and
@@ -294,8 +294,10 @@ int oracle_decode(int n, int m, const int32_t *row_ptr, const int32_t *col_idx,
  * optimum is an even-weight vertex.  Let r be the number of positive c_i.
  * r even: z = [c > 0].  r odd: either drop the smallest positive entry i_p or
  * add the largest non-positive entry i_n, whichever costs less; that is, add
- * i_n when c_{i_p} + c_{i_n} > 0 (the printed comparison is read this way, see
- * the design notes), else drop i_p.  Ties pick the lowest index.
+ * i_n when c_{i_p} + c_{i_n} > 0, else drop i_p.  (The printed comparison of
+ * c_{i_p} with c_{i_n} always holds; the appendix's text compares the values
+ * of the two even neighbours, sum_pos + c_{i_n} against sum_pos - c_{i_p},
+ * which is the test used here.)  Ties pick the lowest index.
  */
 int oracle_lp_max(int d, const double *c, double *z)
 {
