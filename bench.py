@@ -145,32 +145,31 @@ def _batcher_comparators(n: int) -> int:
     return c
 
 
-def algorithmic_ops_per_frame_iter(code) -> int:
-    """FP32 operations one ADMM iteration of one frame needs (a fused multiply-add
-    counts 2, a compare/min/max/select 1), from the code's degrees:
-      variable of degree dv (x-update): 2dv (z - lambda/mu, accumulate) + 5;
-      edge (over-relaxed q, v, lambda-update): 5;
-      check of degree d (projection): clip 2d, facet choice 4d, violation sum d,
-      breakpoints d, sort 2*comparators(d), beta candidates 4d + 1 divide, output 3d."""
-    ops = int((2 * code.var_degrees + 5).sum()) + 5 * code.E
+def hand_ops_per_frame_iter(code) -> int:
+    """A hand count of the FP32 operations of one frame-iteration, from the
+    code's degrees (used only for kernels without an instruction-counter
+    capture; a fused multiply-add counts 1):
+      variable of degree dv (x-update): dv (accumulate) + 4;
+      edge (over-relaxed q, v, lambda-update): 4;
+      check of degree d (projection): clip d, facet choice 3d, violation sum d,
+      breakpoints d, sort 2*comparators(d), beta candidates 3d + 1 divide, output 3d."""
+    ops = int((code.var_degrees + 4).sum()) + 4 * code.E
     for d in code.check_degrees.tolist():
-        ops += 15 * d + 2 * _batcher_comparators(d) + 1
+        ops += 12 * d + 2 * _batcher_comparators(d) + 1
     return ops
 
 
-# DRAM traffic of the decode kernel per frame, from one ncu capture of the small
-# bench case (dram__bytes_read.sum + dram__bytes_write.sum over the frames of
-# that launch; traffic grows with the number of frames).  Keyed by a hash of the
-# kernel sources: a changed kernel reports null until it is captured again.
+# Counters of the decode kernels from ncu captures, keyed by code/schedule and by
+# a hash of the kernel sources at capture time (a changed kernel reports null
+# until it is captured again).  Per frame-iteration:
+#   fp32_ops   FP32 lane-operations: sm__sass_thread_inst_executed_op_fp32_pred_on
+#              plus one more lane for every packed FADD2/FMUL2/FFMA2, so an FMA
+#              counts once, against a peak of one operation per FP32 lane per cycle;
+#   warp_inst  warp instructions issued (smsp__inst_executed.sum).
+# traffic: dram__bytes_read.sum + dram__bytes_write.sum of one launch of
+# traffic_frames frames (the bench's full-size launch where it was captured).
 KERNEL_SOURCES = ("lpdec_device.cuh", "lpdec_kclass.cuh", "lpdec_internal.h")
-MEASURED_TRAFFIC = {
-    # "code/schedule": (source hash, bytes per frame per launch, capture)
-    "C1056/resident": ("fd269eab778905c0", (33_912_064 + 1_916_928) / 8000,
-                 "profiles/decode_kernel_resident_C1056_small.md: 8000 frames x 300 iterations in one launch (tile 128 x 2)"),
-    "C1056/streamed": ("fd269eab778905c0", (236_647_680 + 141_243_136) / 8000,
-                 "profiles/decode_kernel_ring_streamed_C1056_small.md: one iteration of 8000 frames per launch "
-                 "(ring kernel, tile 192 x 5, 6 slots)"),
-}
+MEASURED_COUNTERS = {}
 
 
 def kernel_source_hash() -> str:
@@ -183,11 +182,20 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch(key: str, frames: int):
-    rec = MEASURED_TRAFFIC.get(key)
-    if not rec or rec[0] != kernel_source_hash():
+def counters_for(key: str):
+    rec = MEASURED_COUNTERS.get(key)
+    if not rec or rec["hash"] != kernel_source_hash():
         return None
-    return int(rec[1] * frames)
+    return rec
+
+
+def traffic_per_launch(key: str, frames: int):
+    """DRAM bytes of one launch of `frames` frames, from the capture: exact when
+    the capture ran the same number of frames, else scaled by the frames."""
+    rec = counters_for(key)
+    if not rec or "traffic" not in rec:
+        return None
+    return int(rec["traffic"] * frames / rec["traffic_frames"])
 
 
 def measured_peaks():
@@ -868,27 +876,41 @@ def main():
     if args.schedule in ("resident", "auto"):
         # State stays in shared memory for all 300 iterations: the kernel is bound
         # by instruction issue, not HBM.  Peak: 152 SMs x 128 FP32 lanes x the
-        # maximum SM clock; work: the method's FP32 operations (one lane each).
-        ops = algorithmic_ops_per_frame_iter(code)
+        # maximum SM clock; work: the FP32 lane-operations one frame-iteration
+        # executes, from the instruction counters of an ncu capture of this kernel.
         sm_max = float(clocks.get("sm_max_mhz") or 2070.0)
         peak_gops = 152 * 128 * sm_max * 1e6 / 1e9
+        rec = counters_for(f"{code.name}/resident/{args.state}")
+        if rec:
+            ops, ops_src = rec["fp32_ops"], "counted (ncu instruction counters of this kernel)"
+        else:
+            ops, ops_src = hand_ops_per_frame_iter(code), "hand count (no counter capture of this kernel)"
         ach_gops = F * ITERS * ops / (launch_ms / 1000.0) / 1e9
         roofline = {
             "bound": "alu", "achieved": round(ach_gops, 1), "peak": round(peak_gops, 1), "unit": "Gop/s",
-            "frac": round(ach_gops / peak_gops, 4), "traffic": traffic_per_launch(f"{code.name}/resident", F), "kernel": kname,
-            "note": f"{ops} algorithmic FP32 ops per frame-iteration x {F} frames x {ITERS} iterations per "
-                    f"launch; peak = 152 SMs x 128 lanes x {sm_max:.0f} MHz",
+            "frac": round(ach_gops / peak_gops, 4), "traffic": traffic_per_launch(f"{code.name}/resident/{args.state}", F),
+            "kernel": kname,
+            "note": f"{ops} FP32 lane-operations per frame-iteration ({ops_src}; an FMA counts once) x {F} frames x "
+                    f"{ITERS} iterations per launch; peak = 152 SMs x 128 FP32 lanes x {sm_max:.0f} MHz, of measured "
+                    "maximum SM clock",
             "hbm_effective": {"achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                               "frac": round(achieved / hbm_peak, 4),
                               "note": f"algorithmic bytes {B} per frame-iteration over the {peak_kind} HBM copy "
                                       "bandwidth; an effective figure, since z/lambda/x never leave the SM"},
         }
+        if rec:
+            peak_wi = 152 * 4 * sm_max * 1e6 / 1e9
+            ach_wi = F * ITERS * rec["warp_inst"] / (launch_ms / 1000.0) / 1e9
+            roofline["issue"] = {"achieved": round(ach_wi, 1), "peak": round(peak_wi, 1), "unit": "G warp-inst/s",
+                                 "frac": round(ach_wi / peak_wi, 4),
+                                 "note": f"{rec['warp_inst']} warp instructions per frame-iteration (counted) over "
+                                         "4 issue slots per SM per cycle"}
     else:
         Bm = moved_bytes_per_frame_iter(code, state_bytes)
         moved = F * (ITERS // launches_per_step) * Bm / (launch_ms / 1000.0) / 1e9
         roofline = {
             "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-            "frac": round(achieved / hbm_peak, 4), "traffic": traffic_per_launch(f"{code.name}/streamed", F), "kernel": kname,
+            "frac": round(achieved / hbm_peak, 4), "traffic": traffic_per_launch(f"{code.name}/streamed/{args.state}", F), "kernel": kname,
             "note": f"peak is the {peak_kind} HBM copy bandwidth; algorithmic bytes {B} per frame-iteration "
                     f"x {F} frames x {ITERS // launches_per_step} iterations per launch (they count x written and "
                     f"read once, 8N bytes, which the fused kernel keeps in shared memory, so frac can exceed 1)",

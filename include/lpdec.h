@@ -18,8 +18,10 @@
  *   - Decode calls that take a stream are stream-ordered and asynchronous:
  *     they return after enqueuing work on that stream; synchronize the stream
  *     before reading outputs.  stream == NULL means the legacy default stream.
- *   - All arithmetic on the GPU is FP32.  FP64 is used only to sum the
- *     per-frame residual norms of the stopping test.
+ *   - All ADMM arithmetic on the GPU is FP32; FP64 is used there only to sum
+ *     the per-frame residual norms of the stopping test.  The dual subgradient
+ *     decoder (lpdec_decode_dual) works on integers, after computing each
+ *     variable's Heaviside threshold ceil(-gamma_i/mu) once per frame in FP64.
  *   - Layouts are row-major: an LLR or x batch is [n_frames x n], frame f at
  *     element offset f*n.
  *   - Threads: decode calls on the same code from several host threads (and
@@ -204,8 +206,9 @@ LPDEC_API int lpdec_get_tile(const lpdec_code *code, int32_t state_dtype, int32_
  * max_iter < 1, cert_tol outside (0, 0.5), an unknown state_dtype/schedule,
  * iters_per_launch < 1, or a RESIDENT schedule whose frame state does not fit
  * in shared memory; LPDEC_ENOMEM / LPDEC_ECUDA when workspace allocation or a
- * launch fails.  The call allocates its device workspace stream-ordered
- * (cudaMallocAsync) and frees it the same way.
+ * launch fails.  The call allocates its device workspace stream-ordered from
+ * the library's memory pool (see lpdec_release_memory) and frees it the same
+ * way.
  */
 LPDEC_API int lpdec_decode(const lpdec_code *code, int32_t n_frames, const float *llr,
                  const lpdec_params *params, float *x_out, uint8_t *bits_out,
@@ -309,7 +312,8 @@ LPDEC_API int lpdec_decode_noalloc(const lpdec_code *code, int32_t n_frames, con
 LPDEC_API int lpdec_server_create(size_t device_budget_bytes, void *cuda_stream, lpdec_server **out);
 
 /* Register a code; *code_id indexes it in later submits.  The code must
- * outlive the server. */
+ * outlive the server.  Codes may be added at any time, also while requests of
+ * other codes are in flight; a new code joins the scheduler's next round. */
 LPDEC_API int lpdec_server_add_code(lpdec_server *server, const lpdec_code *code, int32_t *code_id);
 
 /*

@@ -1202,8 +1202,15 @@ __global__ void __launch_bounds__(MAXT, 1) decode_kernel_ring(const DecodeArgs a
         // or already past this one.  So first wait until the slot's tag reads
         // `my`: the producer writes it before publishing, and publishes `my`
         // only after my - R was released, so the slot is then in this round or
-        // just past it, which the parity wait tells apart.
-        if (t == 0) sm.flags[3] = (ring_wait_tag(&meta[s].seq, my) && mbar_wait_bounded(&meta[s].full, ph)) ? 1 : 0;
+        // just past it, which the parity wait tells apart.  After the wait the
+        // tag must still read `my` (the producer retags the slot only after this
+        // group releases it); a mismatch is a broken invariant and stops the
+        // group like a timeout.
+        if (t == 0)
+            sm.flags[3] = (ring_wait_tag(&meta[s].seq, my) && mbar_wait_bounded(&meta[s].full, ph) &&
+                           *reinterpret_cast<const volatile int *>(&meta[s].seq) == my)
+                              ? 1
+                              : 0;
         group_sync(bar, T);
         if (sm.flags[3] == 0) {
             if (t == 0) {

@@ -2,12 +2,14 @@
 // device memory while they run.
 //
 // lpdec_decode takes its scratch space (work-queue counters and, for the
-// STREAMED schedule, the parked w/lambda state) from cudaMallocAsync on every
-// call.  Some callers cannot do that: a receive loop with a fixed memory
-// footprint and a latency budget that rules out allocator calls, or a host
-// framework that owns all device memory through its own allocator and forbids
-// side allocations.  This entry point runs the same kernels with their
-// scratch in one fixed, file-scope device array instead.
+// STREAMED schedule, the parked w/lambda state) from the library's
+// stream-ordered memory pool on every call: an allocator call each time, and
+// pool memory that stays mapped until lpdec_release_memory trims it.  Some
+// callers cannot allow either: a receive loop with a fixed memory footprint
+// and a latency budget that rules out allocator calls, or a host framework
+// that owns all device memory through its own allocator and forbids side
+// allocations.  This entry point runs the same kernels with their scratch in
+// one fixed, file-scope device array instead, and makes no allocator call.
 //
 // The array is kLpdecNoallocScratchBytes (32 MiB) and every GPU that loads this
 // library keeps it until the process exits.  It is shared by every call: the

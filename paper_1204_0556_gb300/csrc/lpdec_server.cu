@@ -232,12 +232,19 @@ int pool_alloc(lpdec_server *sv, Pool &P, int slots) {
 }
 
 // One scheduling round.  Returns an LPDEC status; the caller holds no lock.
+// lpdec_server_add_code may append to sv->pools at any time (under the lock),
+// so the round works on a copy of the pool pointers taken under the lock in
+// step 1; the Pool objects themselves never move.  A code added meanwhile
+// joins the next round.
 int run_round(lpdec_server *sv) {
     const auto t_round = Clock::now();
+    std::vector<Pool *> pools;
     // ---- 1. admission (under the lock)
     {
         std::lock_guard<std::mutex> lk(sv->mu);
-        for (auto &pp : sv->pools) {
+        pools.reserve(sv->pools.size());
+        for (auto &pp : sv->pools) pools.push_back(pp.get());
+        for (Pool *pp : pools) {
             Pool &P = *pp;
             P.n_new = 0;
             const int n = P.code->n;
@@ -261,7 +268,7 @@ int run_round(lpdec_server *sv) {
     // ---- 2. device work for every pool with frames in flight, each on its own
     // stream so the codes' launches overlap
     cudaError_t err;
-    for (auto &pp : sv->pools) {
+    for (Pool *pp : pools) {
         Pool &P = *pp;
         P.timed = false;
         if (P.active.empty()) continue;
@@ -305,7 +312,7 @@ int run_round(lpdec_server *sv) {
         if (err != cudaSuccess) return cuda_error(err, "server: status copy");
     }
     float gpu_ms = 0.0f;
-    for (auto &pp : sv->pools) {
+    for (Pool *pp : pools) {
         Pool &P = *pp;
         if (!P.timed) continue;
         err = cudaStreamSynchronize(P.stream);
@@ -315,9 +322,9 @@ int run_round(lpdec_server *sv) {
         gpu_ms = std::max(gpu_ms, ms);  // the codes overlap: the round takes its slowest code
     }
     // ---- 3. finished frames: gather and copy their outputs
-    std::vector<int> nfin(sv->pools.size(), 0);
-    for (size_t pi = 0; pi < sv->pools.size(); ++pi) {
-        Pool &P = *sv->pools[pi];
+    std::vector<int> nfin(pools.size(), 0);
+    for (size_t pi = 0; pi < pools.size(); ++pi) {
+        Pool &P = *pools[pi];
         const int na = (int)P.active.size();
         int nf = 0;
         for (int i = 0; i < na; ++i)
@@ -336,9 +343,9 @@ int run_round(lpdec_server *sv) {
         if (err == cudaSuccess) err = cudaMemcpyAsync(P.h_co, P.d_co, (size_t)nf, cudaMemcpyDeviceToHost, st);
         if (err != cudaSuccess) return cuda_error(err, "server: output copy");
     }
-    for (size_t pi = 0; pi < sv->pools.size(); ++pi) {
+    for (size_t pi = 0; pi < pools.size(); ++pi) {
         if (!nfin[pi]) continue;
-        err = cudaStreamSynchronize(sv->pools[pi]->stream);
+        err = cudaStreamSynchronize(pools[pi]->stream);
         if (err != cudaSuccess) return cuda_error(err, "server: output gather");
     }
     // ---- 4. hand results to their requests (under the lock)
@@ -346,8 +353,8 @@ int run_round(lpdec_server *sv) {
         std::lock_guard<std::mutex> lk(sv->mu);
         const auto now = Clock::now();
         bool any_done = false;
-        for (size_t pi = 0; pi < sv->pools.size(); ++pi) {
-            Pool &P = *sv->pools[pi];
+        for (size_t pi = 0; pi < pools.size(); ++pi) {
+            Pool &P = *pools[pi];
             const int nf = nfin[pi];
             if (!nf) continue;
             const int n = P.code->n;

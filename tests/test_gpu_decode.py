@@ -118,10 +118,12 @@ def test_c1056_full_bench_size(gpu, oracle_mod, c1056):
     """The bench's workload at full size: 4 x 10^4 frames (10^4 at each of 1.5,
     2.0, 2.5 and 3.0 dB, LLR seeds 100..103), 300 fixed iterations, in the
     bench's RESIDENT launch configuration (6 groups of 160 threads per CTA).
-    Sampled frames equal the oracle's decodes of the same frames (frames are
-    decoded independently, so the oracle runs them alone), and the whole batch
-    through the STREAMED ring kernel (one launch per iteration) equals the
-    RESIDENT decode bit for bit, every frame finished."""
+    The oracle decodes the whole population (Algorithm 1 per frame, FP64):
+    every frame's x is within 1e-4 of it, bits, certificates and syndromes
+    agree on every clean frame, and at each Eb/N0 the GPU's word error rate and
+    certified fraction lie inside the binomial 95% interval of the oracle's.
+    The whole batch through the STREAMED ring kernel (one launch per iteration)
+    equals the RESIDENT decode bit for bit, every frame finished."""
     import torch
 
     per = 10_000
@@ -144,10 +146,15 @@ def test_c1056_full_bench_size(gpu, oracle_mod, c1056):
 
         a = run("resident")
         assert np.all(a["iters"] == 300)
-        rng = np.random.default_rng(17)
-        sample = np.sort(np.concatenate([p * per + rng.choice(per, 6, replace=False) for p in range(4)]))
-        ref = oracle_decode(oracle_mod, c1056, llr[sample], mu=MU, rho=RHO, eps=0.0, max_iter=300)
-        assert_parity(c1056, {k: v[sample] for k, v in a.items()}, ref, 1e-4)
+        ref = oracle_decode(oracle_mod, c1056, llr, mu=MU, rho=RHO, eps=0.0, max_iter=300)
+        assert_parity(c1056, a, ref, 1e-4)
+        for p, snr in enumerate((1.5, 2.0, 2.5, 3.0)):
+            sl = slice(p * per, (p + 1) * per)
+            for name, got_k, ref_k in (("wer", a["bits"][sl].any(axis=1).sum(), ref["bits"][sl].any(axis=1).sum()),
+                                       ("certified", a["cert"][sl].sum(), ref["cert"][sl].sum())):
+                lo, hi = _wilson(int(ref_k), per)
+                print(f"C1056 {snr} dB {name}: GPU {got_k / per:.4f}, oracle {ref_k / per:.4f} [{lo:.4f}, {hi:.4f}]")
+                assert lo <= got_k / per <= hi, (snr, name)
         b = run("streamed")
         for k in a:
             assert np.array_equal(a[k], b[k]), k
@@ -196,25 +203,34 @@ def test_fp16_state(gpu, oracle_mod, c1056, snr, seed):
     assert np.array_equal(got["bits"][clean], ref["bits"][clean])
 
 
-@pytest.mark.parametrize("snr,seed", [(2.5, 202), (1.5, 303)])
-def test_bf16_state(gpu, oracle_mod, c1056, snr, seed):
-    """BF16 storage keeps 8 mantissa bits of lambda/mu, so frames that do not converge
-    drift up to a few 1e-2 from the FP64 trajectory (an FP64 emulation of the rounding
-    shows the same).  Frames the oracle certifies stay within 5e-3, the all-frame
-    bound is 6e-2, and the word error rate stays inside the oracle's 95% interval."""
-    llr = I.awgn_llr(c1056, snr, 160, seed)
+@pytest.mark.parametrize("name,hseed", [("C1056", 0), ("C4000", 2)])
+@pytest.mark.parametrize("snr,seed", [(2.5, 200), (4.0, 201)])
+@pytest.mark.parametrize("state", ["bf16", "f16"])
+def test_16bit_state_error_stated(gpu, oracle_mod, name, hseed, snr, seed, state):
+    """BF16 and FP16 storage of the edge state (FP32 arithmetic) against the FP64
+    oracle, on the precision workload's codes and Eb/N0 points.  On frames that
+    do not converge the FP64 trajectory is sensitive to every rounding, and a
+    16-bit float's rounding of w and lambda/mu (relative 2^-9 for BF16, 2^-12 for
+    FP16) moves x by more than 5e-3 on some frames (an FP64 emulation of the same
+    storage rounding moves them as much), so these formats carry a per-result
+    error statement, not the 5e-3 parity bound.  What holds for them: frames the
+    oracle certifies are within 5e-3, and the word error rate lies in the
+    binomial 95% interval of the oracle's."""
+    code = I.benchmark_code(name, hseed)
+    F = 48
+    llr = I.awgn_llr(code, snr, F, seed)
     kw = dict(mu=MU, rho=RHO, eps=0.0, max_iter=300)
-    got = gpu_decode(gpu, c1056, llr, state="bf16", **kw)
-    ref = oracle_decode(oracle_mod, c1056, llr, **kw)
+    got = gpu_decode(gpu, code, llr, state=state, **kw)
+    ref = oracle_decode(oracle_mod, code, llr, **kw)
     err = np.abs(got["x"] - ref["x"]).max(axis=1)
-    print(f"bf16 at {snr} dB: max|x - x_oracle| = {err.max():.3e}, "
-          f"certified frames {err[ref['cert'] == 1].max(initial=0):.3e}")
-    assert err.max() <= 6e-2
-    assert err[ref["cert"] == 1].max(initial=0.0) <= 5e-3
+    cert = ref["cert"] == 1
+    print(f"{state} {name} {snr} dB: max|x - x_oracle| all {err.max():.3e}, certified {err[cert].max(initial=0):.3e}, "
+          f"frames above 5e-3: {(err > 5e-3).sum()}/{F}")
+    assert err[cert].max(initial=0.0) <= 5e-3
     k_gpu = int(got["bits"].any(axis=1).sum())
     k_ref = int(ref["bits"].any(axis=1).sum())
-    lo, hi = _wilson(k_ref, len(llr))
-    assert lo <= k_gpu / len(llr) <= hi
+    lo, hi = _wilson(k_ref, F)
+    assert lo <= k_gpu / F <= hi
 
 
 @pytest.mark.parametrize("state", ["f32", "bf16", "f16"])

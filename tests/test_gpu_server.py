@@ -51,6 +51,73 @@ def test_results_identical_alone_and_in_the_mix(gpu, server_codes):
             assert np.array_equal(got[k], ref[k]), (codes[c].name, k)
 
 
+def test_served_frames_match_the_oracle(gpu, oracle_mod, server_codes):
+    """Served frames against the FP64 oracle directly (Algorithm 1 per frame):
+    fixed-iteration requests of three codes arrive while others are in flight;
+    every frame's x is within 1e-4 of the oracle's decode of that frame, and
+    bits, certificates and syndromes agree on frames with no oracle entry near
+    1/2 or the certificate bound."""
+    from test_gpu_decode import assert_parity, oracle_decode
+
+    codes, handles = server_codes
+    kw = dict(mu=3.0, rho=1.9, eps=0.0, max_iter=120)
+    p = gpu.make_params(iters_per_launch=8, **kw)
+    srv = gpu.Server(budget_bytes=2 << 30)
+    try:
+        ids = [srv.add_code(h) for h in handles[:3]]
+        rng = np.random.default_rng(21)
+        plan = []
+        for r in range(24):
+            c = int(rng.integers(0, 3))
+            llr = I.awgn_llr(codes[c], float(rng.uniform(1.5, 4.0)), 2, 7000 + r)
+            plan.append((c, llr, srv.submit(ids[c], llr, p)))
+            if r % 5 == 0:
+                time.sleep(0.002)
+        results = [srv.poll(rid, ids[c], len(llr), timeout_ms=60_000) for c, llr, rid in plan]
+    finally:
+        srv.close()
+    for c in range(3):
+        got_parts = [g for (cc, _, _), g in zip(plan, results) if cc == c]
+        if not got_parts:
+            continue
+        llr = np.concatenate([l for cc, l, _ in plan if cc == c])
+        got = {k: np.concatenate([g[k] for g in got_parts]) for k in ("x", "bits", "iters", "cert")}
+        ref = oracle_decode(oracle_mod, codes[c], llr, **kw)
+        assert_parity(codes[c], got, ref, 1e-4, min_clean=0.3)
+
+
+def test_add_code_while_frames_in_flight(gpu, server_codes):
+    """Codes may be added while the scheduler runs rounds for others: the
+    round works on its own copy of the pool list, so the list growing (and
+    reallocating) under it is harmless, and the new codes join later rounds.
+    Every result still equals lpdec_decode of the frame alone."""
+    from test_gpu_decode import gpu_decode
+
+    codes, handles = server_codes
+    p = gpu.make_params(mu=3.0, rho=1.9, eps=1e-5, max_iter=300, iters_per_launch=4)
+    srv = gpu.Server(budget_bytes=6 << 30)
+    try:
+        first = srv.add_code(handles[1])
+        plan = []
+        for r in range(16):
+            llr = I.awgn_llr(codes[1], 1.5, 8, 8100 + r)
+            plan.append((first, 1, llr, srv.submit(first, llr, p)))
+        # twelve more pools, added one by one between submits while C1056 frames run
+        for k in range(12):
+            c = (0, 2, 1)[k % 3]
+            cid = srv.add_code(handles[c])
+            llr = I.awgn_llr(codes[c], 2.5, 2, 8200 + k)
+            plan.append((cid, c, llr, srv.submit(cid, llr, p)))
+        results = [srv.poll(rid, cid, len(llr), timeout_ms=120_000) for cid, _, llr, rid in plan]
+    finally:
+        srv.close()
+    for (cid, c, llr, _), got in zip(plan, results):
+        assert got is not None
+        ref = gpu_decode(gpu, codes[c], llr, mu=3.0, rho=1.9, eps=1e-5, max_iter=300)
+        for k in ("x", "bits", "iters", "cert"):
+            assert np.array_equal(got[k], ref[k]), (codes[c].name, k)
+
+
 def test_poll_timeout_and_errors(gpu, server_codes):
     codes, handles = server_codes
     p = gpu.make_params(eps=0.0, max_iter=1000, iters_per_launch=4)
