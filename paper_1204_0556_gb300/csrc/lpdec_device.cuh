@@ -27,6 +27,22 @@
 
 namespace lpdec {
 
+// Lanes per check in the decode kernel of a class: one thread per check for
+// D <= 8 (sorted breakpoints), L adjacent lanes for wider checks
+// (check_update_w).
+#ifndef LPDEC_L16
+#define LPDEC_L16 2
+#endif
+#ifndef LPDEC_L20
+#define LPDEC_L20 2
+#endif
+#ifndef LPDEC_L32
+#define LPDEC_L32 2
+#endif
+__host__ __device__ constexpr int class_lanes(int D) {
+    return D <= 8 ? 1 : (D <= 16 ? LPDEC_L16 : (D <= 20 ? LPDEC_L20 : LPDEC_L32));
+}
+
 constexpr float kPadV = -1.0e30f;  // value of an unused lane of a check (clips to 0)
 constexpr float kBigKappa = 1.0e30f;
 
@@ -119,33 +135,6 @@ __device__ __forceinline__ float beta_sorted(float (&kap)[D], int d) {
     return fmaxf(best, 0.0f);
 }
 
-// Michelot-style fixed point for large D (no sort, no kappa array): start
-// from all entries active and drop those with kappa >= beta until the active
-// set is stable.  The iterates decrease monotonically to beta* in at most d
-// passes.  kappa_k = v_k - 1 on the facet set (bit k of th), -v_k off it.
-template <int D>
-__device__ __forceinline__ float beta_fixed_point(const float (&v)[D], int d, unsigned th) {
-    float s = 1.0f;
-#pragma unroll
-    for (int k = 0; k < D; ++k)
-        if (k < d) s += ((th >> k) & 1u) ? v[k] - 1.0f : -v[k];
-    float beta = __fdividef(s, (float)d);
-    for (int it = 0; it < D; ++it) {
-        float s2 = 1.0f;
-        int cnt = 0;
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-            const float kap = ((th >> k) & 1u) ? v[k] - 1.0f : -v[k];
-            if (k < d && kap < beta) { s2 += kap; ++cnt; }
-        }
-        if (cnt == 0) break;
-        const float nb = __fdividef(s2, (float)cnt);
-        if (!(nb < beta)) break;
-        beta = nb;
-    }
-    return fmaxf(beta, 0.0f);
-}
-
 // ---------------------------------------------------------------------------
 // Euclidean projection of v (entries k < d; entries k >= d must hold kPadV)
 // onto the parity polytope PP_d (Section 4.4, Algorithm 2).
@@ -170,14 +159,6 @@ struct Proj {
 __device__ __forceinline__ float proj_z(float v, const Proj &pr, int k) {
     return __saturatef(((pr.facet >> k) & 1u) ? v - pr.beta : v + pr.beta);
 }
-// The same z with bit k of the facet moved into the sign of beta (v + (-beta)
-// rounds as v - beta): one add instead of a choice between two.  Faster in the
-// segmented wide-check update, slower in the thread-per-check one.
-__device__ __forceinline__ float proj_z_signed(float v, const Proj &pr, int k) {
-    const unsigned sgn = (pr.facet << (31 - k)) & 0x80000000u;
-    return __saturatef(v + __int_as_float(__float_as_int(pr.beta) ^ sgn));
-}
-
 //
 // Facet and violation test in one pass.  With zh = clip(v) and
 // delta_k = |zh_k - 1/2|, zh_k = 1/2 + delta_k on S and 1/2 - delta_k off S, so
@@ -190,8 +171,8 @@ __device__ __forceinline__ float proj_z_signed(float v, const Proj &pr, int k) {
 // bits are tied and the lowest index wins.
 template <int D>
 __device__ __forceinline__ Proj project_pp(const float (&v)[D], int d) {
-    static_assert(D >= 1 && D <= 32, "check degree above 32");
-    constexpr int kIdxBits = D <= 8 ? 3 : 5;
+    static_assert(D >= 1 && D <= 8, "wider checks use project_wide");
+    constexpr int kIdxBits = 3;
     constexpr int kIdxMask = (1 << kIdxBits) - 1;
     unsigned th = 0u;
     int key = 0x7fffffff;
@@ -228,7 +209,7 @@ __device__ __forceinline__ Proj project_pp(const float (&v)[D], int d) {
     pr.beta = 0.0f;
     if (sdist <= 0.5f * (float)d - 1.0f) return pr;  // zh already in PP_d
 
-    if constexpr (D <= 8) {
+    {
         float kap[D];
 #pragma unroll
         for (int k = 0; k < D; ++k)
@@ -246,8 +227,6 @@ __device__ __forceinline__ Proj project_pp(const float (&v)[D], int d) {
         }
         const float c1 = 1.0f + k1;
         pr.beta = k2 >= c1 ? fmaxf(c1, 0.0f) : beta_sorted<D>(kap, d);
-    } else {
-        pr.beta = beta_fixed_point<D>(v, d, th);
     }
     return pr;
 }
@@ -450,46 +429,137 @@ __device__ __forceinline__ void check_update(const CodeView &c, const IterCfg &p
     }
 }
 
-// Segmented check update: L lanes (L = 2, 4, ..., 32, aligned within the
-// warp) share one check; lane r of the segment holds entries r, r+L, r+2L, ...
-// (V = ceil(D/L) registers per lane).  The facet choice, the violation test
-// and the beta fixed point reduce over the segment with xor-shuffles.  Every
-// lane of the warp must call this with the same loop trip counts; a lane whose
-// check index is out of range passes valid = false and does no stores.
+// Check update for wide checks (D > 8): L = 1 or 2 adjacent lanes per check,
+// lane r holding entries r, r + L, r + 2L, ... in registers (V = D / L of
+// them), so every load and store is at a compile-time offset from the check's
+// first edge and the lanes combine their partial results with one xor-shuffle
+// each.  Entries q >= d hold kPadV: they clip to 0, are never in the facet set,
+// and their breakpoint is +1e30, so they never become active.
+//
+// After the facet choice the registers hold the breakpoints kappa_q = v_q - 1
+// on the facet set and -v_q off it; v and z are rebuilt from kappa: v = kappa + 1,
+// z = clip(v - beta) on the set; v = -kappa, z = clip(v + beta) off it.  beta*
+// solves sum_q max(0, beta - kappa_q) = 1 (see beta_sorted): h(beta) =
+// sum_q max(0, beta - kappa_q) - 1 is convex and increasing, so Newton's step
+// beta <- (1 + sum_{kappa < beta} kappa) / #{kappa < beta} from any point above
+// the root decreases monotonically to it (the tangent lies below h) and stops
+// when the active set stops changing.  It starts from the smaller of two
+// points above the root: (1 + sum_q kappa_q) / d, exact when every breakpoint
+// is active, and 1 + kappa_(1), exact when only the smallest one is.
+// DV > 0: the regular form (16-bit column indices; with FP32 state and no
+// residuals ws holds u = rho x + (1 - rho) w, see frame_run).  Check j's
+// edges start at j*reg_dc when every check has degree reg_dc, else at
+// row_ptr[j].  Both lanes of a pair must call this with the same j; a pair
+// whose check index is out of range passes valid = false and stores nothing.
+// Reductions over the L adjacent lanes (L = 1, 2 or 4) that share a check.
 template <int L>
-__device__ __forceinline__ float seg_sum(float x) {
+__device__ __forceinline__ float pair_sum(float x) {
 #pragma unroll
     for (int o = 1; o < L; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     return x;
 }
 template <int L>
-__device__ __forceinline__ int seg_sum_i(int x) {
+__device__ __forceinline__ int pair_sum_i(int x) {
 #pragma unroll
     for (int o = 1; o < L; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     return x;
 }
-
 template <int L>
-__device__ __forceinline__ int seg_min_i(int x) {
+__device__ __forceinline__ int pair_min_i(int x) {
 #pragma unroll
     for (int o = 1; o < L; o <<= 1) x = min(x, __shfl_xor_sync(0xffffffffu, x, o));
     return x;
 }
+template <int L>
+__device__ __forceinline__ float pair_min(float x) {
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1) x = fminf(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
 
-// v = rho x + (1 - rho) w + (2 - rho) lambda/mu (z_old is not formed); when
-// need_res, the residual terms re-read the old w and lambda/mu before they are
-// overwritten.  (One instantiation with a runtime flag: two inlined copies of
-// this update exceed the 64-register budget of the 1024-thread kernel.)
-// DV > 0: every variable has degree DV: 16-bit column indices, and in
-// iterations without residuals with FP32 state ws holds u = rho x + (1 - rho) w
-// (see frame_run).  Check j's edges start at j*reg_dc when every check has
-// degree reg_dc, else at row_ptr[j].
-template <int D, int L, int DV, typename S>
-__device__ __forceinline__ void check_update_seg(const CodeView &c, const IterCfg &p, int j, bool valid,
-                                                 S *ws, S *ls, const float *xs, bool need_res,
-                                                 float &rp, float &rd) {
-    static_assert(D <= 32, "packed facet keys hold a 5-bit entry index");
-    constexpr int V = (D + L - 1) / L;
+// The projection of one wide check.  On entry kap[k] holds v of this lane's
+// entry q = k*L + r (kPadV for q >= d; dr = d - r); on return it holds the
+// breakpoint kappa_q, bit k of th marks the facet set, and the result is beta
+// (0 when clip(v) is already in PP_d).  Every lane of the warp must call this
+// (the pair reductions are warp-wide shuffles); a pair with d = 0 does no work
+// that matters.
+template <int D, int L>
+__device__ __forceinline__ float project_wide(float (&kap)[D / L], int d, int dr, int r, unsigned &th_out) {
+    constexpr int V = D / L;
+    // facet S = {v > 1/2}, the entry closest to 1/2 flipped when |S| is even;
+    // violation test sum_q |clip(v_q) - 1/2| (- 2 min when flipped) > d/2 - 1.
+    // Padded entries add 1/2 each to the sum, as they do to the right side
+    // (taken over all D entries).  Keys hold the entry index q = k*L + r.
+    unsigned th = 0u;  // bit k: this lane's entry k is in the facet set
+    int key = 0x7fffffff;
+    float sdist = 0.0f;
+#pragma unroll
+    for (int k = 0; k < V; k += 2) {
+        const float a = kap[k], b = k + 1 < V ? kap[k + 1] : kPadV;
+        if (a > 0.5f) th |= 1u << k;
+        if (b > 0.5f) th |= 1u << (k + 1);
+        const float2 t2 = __fadd2_rn(make_float2(__saturatef(a), __saturatef(b)), make_float2(-0.5f, -0.5f));
+        sdist += fabsf(t2.x);
+        key = min(key, (__float_as_int(t2.x) & 0x7fffffe0) | (k * L + r));
+        if (k + 1 < V) {
+            sdist += fabsf(t2.y);
+            key = min(key, (__float_as_int(t2.y) & 0x7fffffe0) | ((k + 1) * L + r));
+        }
+    }
+    key = pair_min_i<L>(key);
+    sdist = pair_sum<L>(sdist);
+    if ((pair_sum_i<L>(__popc(th)) & 1) == 0) {
+        const int qb = key & 31;
+        if (qb % L == r) th ^= 1u << (qb / L);
+        sdist -= 2.0f * __int_as_float(key & ~31);
+    }
+    const bool violated = d > 0 && sdist > 0.5f * (float)D - 1.0f;
+    // breakpoints in place; their sum over the real entries, and the smallest
+    float ksum = 0.0f, k1 = kBigKappa;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        kap[k] = ((th >> k) & 1u) ? kap[k] - 1.0f : -kap[k];
+        if (k * L < dr) ksum += kap[k];
+        k1 = fminf(k1, kap[k]);
+    }
+    ksum = pair_sum<L>(ksum);
+    k1 = pair_min<L>(k1);
+    th_out = th;
+    float beta = 0.0f;
+    if (violated) {  // the same for both lanes of a pair
+        const unsigned pm = ((1u << L) - 1u) << (threadIdx.x & (32 - L));  // the check's lanes
+        beta = fminf(__fdividef(1.0f + ksum, (float)d), 1.0f + k1);
+        for (int it = 0; it <= D; ++it) {
+            float s1 = 0.0f;
+            int cnt = 0;
+#pragma unroll
+            for (int k = 0; k < V; ++k)
+                if (kap[k] < beta) { s1 += kap[k]; ++cnt; }
+#pragma unroll
+            for (int o = 1; o < L; o <<= 1) {
+                s1 += __shfl_xor_sync(pm, s1, o);
+                cnt += __shfl_xor_sync(pm, cnt, o);
+            }
+            const float nb = __fdividef(1.0f + s1, (float)cnt);  // cnt >= 1: beta > kappa_(1)
+            if (!(nb < beta)) break;
+            beta = nb;
+        }
+        beta = fmaxf(beta, 0.0f);
+    }
+    return beta;
+}
+
+// v and z of entry k after project_wide.
+__device__ __forceinline__ void wide_vz(float kap, bool on, float beta, float &v, float &z) {
+    v = on ? kap + 1.0f : -kap;
+    z = __saturatef(on ? v - beta : v + beta);
+}
+
+template <int D, int L, int DV, typename S, bool RES>
+__device__ __forceinline__ void check_update_w(const CodeView &c, const IterCfg &p, int j, bool valid, S *ws, S *ls,
+                                               const float *xs, float &rp, float &rd) {
+    static_assert(D > 8 && D <= 32 && (L == 1 || L == 2 || L == 4) && D % L == 0, "wide class");
+    constexpr int V = D / L;
     const int r = threadIdx.x & (L - 1);
     int e0 = 0, d = 0;
     if (valid) {
@@ -505,133 +575,44 @@ __device__ __forceinline__ void check_update_seg(const CodeView &c, const IterCf
         if constexpr (DV > 0) return c.col16[e];
         else return __ldg(c.col_idx + e);
     };
-    const bool folded = kFoldX<S> && DV > 0 && !need_res;
-    float v[V];
+    constexpr bool kFold = kFoldX<S> && DV > 0 && !RES;
+    const int eb = e0 + r;   // this lane's first entry; entry k of the lane is edge eb + k*L
+    const int dr = d - r;    // entry k of the lane is real when k*L < dr
+    const S *wsj = ws + eb;
+    const S *lsj = ls + eb;
+    float kap[V];
 #pragma unroll
     for (int k = 0; k < V; ++k) {
-        const int q = k * L + r;
-        if (q < d) {
-            const int e = e0 + q;
-            if (folded) {
-                v[k] = fmaf(p.tmr, ld<S>(ls[e]), ld<S>(ws[e]));
+        if (k * L < dr) {
+            if constexpr (kFold) {
+                kap[k] = fmaf(p.tmr, ld<S>(lsj[k * L]), ld<S>(wsj[k * L]));
             } else {
-                const float xk = xs[col_of(e)];
-                v[k] = fmaf(p.rho, xk, fmaf(p.omr, ld<S>(ws[e]), p.tmr * ld<S>(ls[e])));
+                const float xk = xs[col_of(eb + k * L)];
+                kap[k] = fmaf(p.rho, xk, fmaf(p.omr, ld<S>(wsj[k * L]), p.tmr * ld<S>(lsj[k * L])));
             }
         } else {
-            v[k] = kPadV;
+            kap[k] = kPadV;
         }
     }
-    // facet: S = {zh > 1/2}, flip the entry closest to 1/2 when |S| is even;
-    // violation test sum_k |zh_k - 1/2| (- 2 min when flipped) > d/2 - 1, with
-    // the packed argmin key of project_pp, reduced over the segment.
-    unsigned th = 0u;
-    int key = 0x7fffffff;
-    float sdist = 0.0f;
-    // as in project_pp: v > 1/2 for the set, zh - 1/2 in packed pairs, |.| in the sum and key
-    float tz[V];
+    unsigned th;
+    const float beta = project_wide<D, L>(kap, d, dr, r, th);
+    // z, lambda/mu = v - z and w = z - lambda/mu
 #pragma unroll
     for (int k = 0; k < V; ++k) {
-        if (v[k] > 0.5f) th |= 1u << k;
-        tz[k] = __saturatef(v[k]);
-    }
-#pragma unroll
-    for (int k = 0; k + 1 < V; k += 2) {
-        const float2 t2 = __fadd2_rn(make_float2(tz[k], tz[k + 1]), make_float2(-0.5f, -0.5f));
-        tz[k] = t2.x;
-        tz[k + 1] = t2.y;
-    }
-    if (V & 1) tz[V - 1] = tz[V - 1] - 0.5f;
-#pragma unroll
-    for (int k = 0; k < V; ++k) {
-        const int q = k * L + r;
-        if (q < d) {
-            sdist += fabsf(tz[k]);
-            key = min(key, (__float_as_int(tz[k]) & 0x7fffffe0) | q);
-        }
-    }
-    key = seg_min_i<L>(key);
-    sdist = seg_sum<L>(sdist);
-    const int s = seg_sum_i<L>(__popc(th));
-    if ((s & 1) == 0 && d > 0) {
-        const int kb = key & 31;
-        if ((kb % L) == r) th ^= 1u << (kb / L);
-        sdist -= 2.0f * __int_as_float(key & ~31);
-    }
-    const bool violated = d > 0 && sdist > 0.5f * (float)d - 1.0f;  // else zh is the projection
-    float beta = 0.0f;
-    {
-        // fixed point of sum_k max(0, beta - kappa_k) = 1, from all entries active
-        bool done = !violated;
-        float s1 = 0.0f;
-        int c1 = 0;
-#pragma unroll
-        for (int k = 0; k < V; ++k) {
-            const int q = k * L + r;
-            if (q < d) { s1 += ((th >> k) & 1u) ? v[k] - 1.0f : -v[k]; ++c1; }
-        }
-        s1 = seg_sum<L>(s1);
-        c1 = seg_sum_i<L>(c1);
-        float cur = c1 > 0 ? __fdividef(1.0f + s1, (float)c1) : 0.0f;
-        for (int it = 0; it < D; ++it) {
-            if (__all_sync(0xffffffffu, done)) break;
-            float s2 = 0.0f;
-            int c2 = 0;
-#pragma unroll
-            for (int k = 0; k < V; ++k) {
-                const int q = k * L + r;
-                const float kap = ((th >> k) & 1u) ? v[k] - 1.0f : -v[k];
-                if (q < d && kap < cur) { s2 += kap; ++c2; }
-            }
-            s2 = seg_sum<L>(s2);
-            c2 = seg_sum_i<L>(c2);
-            if (!done) {
-                const float nb = c2 > 0 ? __fdividef(1.0f + s2, (float)c2) : cur;
-                if (c2 == 0 || !(nb < cur)) {
-                    done = true;
-                    beta = fmaxf(cur, 0.0f);
-                } else {
-                    cur = nb;
-                }
-            }
-        }
-        if (!done) beta = fmaxf(cur, 0.0f);
-        if (!violated) beta = 0.0f;
-    }
-    Proj pr;
-    pr.facet = th;
-    pr.beta = beta;
-    // z, then lambda/mu = v - z and w = z - lambda/mu in packed FP32 pairs (each
-    // lane rounds as the subtraction: the product with -1 is exact)
-    float zq[V], lq[V], wq[V];
-#pragma unroll
-    for (int k = 0; k < V; ++k) zq[k] = proj_z_signed(v[k], pr, k);
-#pragma unroll
-    for (int k = 0; k < V; k += 2) {
-        if (k + 1 < V) {
-            const float2 m1 = make_float2(-1.0f, -1.0f), z2 = make_float2(zq[k], zq[k + 1]);
-            const float2 l2 = __ffma2_rn(z2, m1, make_float2(v[k], v[k + 1]));
-            const float2 w2 = __ffma2_rn(l2, m1, z2);
-            lq[k] = l2.x; lq[k + 1] = l2.y; wq[k] = w2.x; wq[k + 1] = w2.y;
-        } else {
-            lq[k] = v[k] - zq[k];
-            wq[k] = zq[k] - lq[k];
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < V; ++k) {
-        const int q = k * L + r;
-        if (q < d) {
-            const int e = e0 + q;
-            const float z = zq[k];
-            if (need_res) {
+        if (k * L < dr) {
+            float v, z;
+            wide_vz(kap[k], (th >> k) & 1u, beta, v, z);
+            const float l = v - z;
+            const float w = z - l;
+            const int e = eb + k * L;
+            if constexpr (RES) {
                 const float a = xs[col_of(e)] - z;
                 const float b = z - (ld<S>(ws[e]) + ld<S>(ls[e]));
                 rp = fmaf(a, a, rp);
                 rd = fmaf(b, b, rd);
             }
-            ls[e] = st<S>(lq[k]);
-            ws[e] = st<S>(wq[k]);
+            ls[e] = st<S>(l);
+            ws[e] = st<S>(w);
         }
     }
 }
@@ -867,17 +848,26 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
         group_sync(bar, T);
         // ---- z- and lambda-updates (Algorithm 1; Section 5.2 over-relaxation)
         float rp = 0.0f, rd = 0.0f;
-        if constexpr (L == 1) {
+        if constexpr (D > 8) {
+            // L lanes per check; every lane of the group runs the same number of passes
+            const int per_pass = T / L;
+            if (need_res) {
+                for (int j0 = 0; j0 < c.m; j0 += per_pass) {
+                    const int j = j0 + t / L;
+                    check_update_w<D, L, DV, S, true>(c, p, j, j < c.m, sm.w, sm.l, sm.x, rp, rd);
+                }
+            } else {
+                for (int j0 = 0; j0 < c.m; j0 += per_pass) {
+                    const int j = j0 + t / L;
+                    check_update_w<D, L, DV, S, false>(c, p, j, j < c.m, sm.w, sm.l, sm.x, rp, rd);
+                }
+            }
+        } else {
+            static_assert(L == 1, "checks of degree <= 8 take one thread each");
             if (need_res) {
                 for (int j = t; j < c.m; j += T) check_update<D, DV, S, true>(c, p, j, sm.w, sm.l, sm.x, rp, rd);
             } else {
                 for (int j = t; j < c.m; j += T) check_update<D, DV, S, false>(c, p, j, sm.w, sm.l, sm.x, rp, rd);
-            }
-        } else {
-            const int per_pass = T / L;
-            for (int j0 = 0; j0 < c.m; j0 += per_pass) {
-                const int j = j0 + t / L;
-                check_update_seg<D, L, DV, S>(c, p, j, j < c.m, sm.w, sm.l, sm.x, need_res, rp, rd);
             }
         }
         ++k;
@@ -1246,19 +1236,44 @@ __global__ void __launch_bounds__(MAXT, 1) decode_kernel_ring(const DecodeArgs a
     if (t == 0) bulk_wait_all();
 }
 
-// Projection of `count` vectors of dimension d (d <= D), one per thread.
+// Projection of `count` vectors of dimension d (d <= D): one thread per vector
+// for D <= 8, the decoder's lane pairs (project_wide) for wider classes, so
+// the results are the decoder's own.
 template <int D>
 __global__ void __launch_bounds__(256) project_kernel(int d, long long count, const float *__restrict__ v,
                                                      float *__restrict__ z) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count) return;
-    float vv[D];
+    constexpr int L = class_lanes(D);
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long i = tid / L;
+    if constexpr (L == 1) {
+        if (i >= count) return;
+        float vv[D];
 #pragma unroll
-    for (int k = 0; k < D; ++k) vv[k] = (k < d) ? v[i * d + k] : kPadV;
-    const Proj pr = project_pp<D>(vv, d);
+        for (int k = 0; k < D; ++k) vv[k] = (k < d) ? v[i * d + k] : kPadV;
+        const Proj pr = project_pp<D>(vv, d);
 #pragma unroll
-    for (int k = 0; k < D; ++k)
-        if (k < d) z[i * d + k] = proj_z(vv[k], pr, k);
+        for (int k = 0; k < D; ++k)
+            if (k < d) z[i * d + k] = proj_z(vv[k], pr, k);
+    } else {
+        // every lane takes part in the pair reductions; out-of-range pairs have d = 0
+        constexpr int V = D / L;
+        const int r = threadIdx.x & (L - 1);
+        const int dd = i < count ? d : 0;
+        const int dr = dd - r;
+        float kap[V];
+#pragma unroll
+        for (int k = 0; k < V; ++k) kap[k] = (k * L < dr) ? v[i * d + k * L + r] : kPadV;
+        unsigned th;
+        const float beta = project_wide<D, L>(kap, dd, dr, r, th);
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            if (k * L < dr) {
+                float vk, zk;
+                wide_vz(kap[k], (th >> k) & 1u, beta, vk, zk);
+                z[i * d + k * L + r] = zk;
+            }
+        }
+    }
 }
 
 }  // namespace lpdec

@@ -20,21 +20,6 @@ inline int degree_class(int max_dc) {
     return -1;
 }
 
-// Lanes per check in the decode kernel of a class: one thread per check for
-// D <= 8 (sorted breakpoints), a segment of lanes for wider checks.
-#ifndef LPDEC_L16
-#define LPDEC_L16 2
-#endif
-#ifndef LPDEC_L20
-#define LPDEC_L20 4
-#endif
-#ifndef LPDEC_L32
-#define LPDEC_L32 4
-#endif
-__host__ __device__ constexpr int class_lanes(int D) {
-    return D <= 8 ? 1 : (D <= 16 ? LPDEC_L16 : (D <= 20 ? LPDEC_L20 : LPDEC_L32));
-}
-
 // Largest CTA the decode kernel of a class is compiled for.
 constexpr int class_max_threads_D(int D) { return 1024; }
 inline int class_max_threads(int cls) { return class_max_threads_D(kClassD[cls]); }

@@ -128,7 +128,8 @@ cudaError_t LPDEC_CAT(launch_project_, LPDEC_D)(int d, long long count, const fl
                                                  cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
     const int block = 256;
-    const long long grid = (count + block - 1) / block;
+    const long long lanes = kL;  // threads per vector (project_kernel)
+    const long long grid = (count * lanes + block - 1) / block;
     project_kernel<kD><<<(unsigned)grid, block, 0, s>>>(d, count, v, z);
     return cudaGetLastError();
 }

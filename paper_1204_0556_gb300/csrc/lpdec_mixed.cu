@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(kMixedMaxThreads, 1) mixed_kernel(const MixedA
                 switch (cur_code.kind) {
                     case kK6R3: mixed_round<6, 1, 3, S>(&cur_code, b, smem_raw, g, t); break;
                     case kK8R4: mixed_round<8, 1, 4, S>(&cur_code, b, smem_raw, g, t); break;
-                    default: mixed_round<32, 4, 3, S>(&cur_code, b, smem_raw, g, t); break;  // kK32R3
+                    default: mixed_round<32, class_lanes(32), 3, S>(&cur_code, b, smem_raw, g, t); break;  // kK32R3
                 }
             } else {
                 switch (cur_code.kind) {
@@ -118,12 +118,12 @@ __global__ void __launch_bounds__(kMixedMaxThreads, 1) mixed_kernel(const MixedA
                     case kK6: mixed_round_call<6, 1, 0, S>(&cur_code, b, smem_raw, g, t); break;
                     case kK8R4: mixed_round_call<8, 1, 4, S>(&cur_code, b, smem_raw, g, t); break;
                     case kK8: mixed_round_call<8, 1, 0, S>(&cur_code, b, smem_raw, g, t); break;
-                    case kK16: mixed_round_call<16, 2, 0, S>(&cur_code, b, smem_raw, g, t); break;
-                    case kK20: mixed_round_call<20, 4, 0, S>(&cur_code, b, smem_raw, g, t); break;
-                    case kK16R3: mixed_round_call<16, 2, 3, S>(&cur_code, b, smem_raw, g, t); break;
-                    case kK20R3: mixed_round_call<20, 4, 3, S>(&cur_code, b, smem_raw, g, t); break;
-                    case kK32R3: mixed_round_call<32, 4, 3, S>(&cur_code, b, smem_raw, g, t); break;
-                    default: mixed_round_call<32, 4, 0, S>(&cur_code, b, smem_raw, g, t); break;
+                    case kK16: mixed_round_call<16, class_lanes(16), 0, S>(&cur_code, b, smem_raw, g, t); break;
+                    case kK20: mixed_round_call<20, class_lanes(20), 0, S>(&cur_code, b, smem_raw, g, t); break;
+                    case kK16R3: mixed_round_call<16, class_lanes(16), 3, S>(&cur_code, b, smem_raw, g, t); break;
+                    case kK20R3: mixed_round_call<20, class_lanes(20), 3, S>(&cur_code, b, smem_raw, g, t); break;
+                    case kK32R3: mixed_round_call<32, class_lanes(32), 3, S>(&cur_code, b, smem_raw, g, t); break;
+                    default: mixed_round_call<32, class_lanes(32), 0, S>(&cur_code, b, smem_raw, g, t); break;
                 }
             }
         }

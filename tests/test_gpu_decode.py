@@ -632,7 +632,11 @@ def _wilson(k, n, z=1.96):
     den = 1 + z * z / n
     c = (p + z * z / (2 * n)) / den
     h = z * np.sqrt(p * (1 - p) / n + z * z / (4 * n * n)) / den
-    return c - h, c + h
+    # k = 0 and k = n put an end of the interval exactly at 0 or 1; keep it
+    # there (the formula rounds it a few ulps inside)
+    lo = 0.0 if k == 0 else c - h
+    hi = 1.0 if k == n else c + h
+    return lo, hi
 
 
 def test_wer_within_oracle_interval(gpu, oracle_mod, c1056):
