@@ -46,12 +46,15 @@ def parse():
     ap.add_argument("--frames-per-point", type=int, default=10_000)
     ap.add_argument("--code", default="C1056", choices=["C96", "C1056", "C2640", "C4000", "C8000"],
                     help="code of the single-code workload (the headline is C1056)")
-    ap.add_argument("--iters", type=int, default=300, help="fixed ADMM iterations of the single-code workload")
+    ap.add_argument("--iters", type=int, default=300, help="fixed ADMM iterations of the single-code workload "
+                    "(with --eps > 0: the most a frame may run)")
+    ap.add_argument("--eps", type=float, default=0.0, help="stopping tolerance of the single-code workload "
+                    "(0: fixed iterations; > 0: per-frame early exit, RESIDENT schedule only)")
     ap.add_argument("--no-autotune", action="store_true", help="use the library's default tile")
     ap.add_argument("--tile", default="", help="GROUP_THREADS,GROUPS[,RING_SLOTS]: set the single-code tile instead of "
                     "autotuning (RING_SLOTS > GROUPS: the STREAMED ring kernel)")
     ap.add_argument("--schedule", default="resident", choices=["resident", "streamed", "auto"])
-    ap.add_argument("--state", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--state", default="f32", choices=["f32", "bf16", "f16", "q16"])
     ap.add_argument("--variants", type=int, default=1, help="also time the other schedules/precisions")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
@@ -261,7 +264,7 @@ class ClockSampler:
                 "samples": int(len(rows)), "power_w_max": max(float(r[3]) for r in rows)}
 
 
-def oracle_sample(code, llr, seconds: float):
+def oracle_sample(code, llr, seconds: float, eps: float = 0.0):
     """Time the FP64 oracle on a bounded, evenly spread sample of the workload."""
     import oracle
 
@@ -270,17 +273,18 @@ def oracle_sample(code, llr, seconds: float):
     F = len(llr)
     probe = np.linspace(0, F - 1, max(threads, 16)).astype(int)
     t0 = time.perf_counter()
-    oracle.decode(code.row_ptr, code.col_idx, code.n, llr[probe].astype(np.float64), mu=MU, rho=RHO, eps=0.0,
+    oracle.decode(code.row_ptr, code.col_idx, code.n, llr[probe].astype(np.float64), mu=MU, rho=RHO, eps=eps,
                   max_iter=ITERS, threads=threads)
     per_frame = (time.perf_counter() - t0) / len(probe)
     n = int(min(F, max(len(probe), seconds / max(per_frame, 1e-9))))
     idx = np.linspace(0, F - 1, n).astype(int)
     t0 = time.perf_counter()
-    oracle.decode(code.row_ptr, code.col_idx, code.n, llr[idx].astype(np.float64), mu=MU, rho=RHO, eps=0.0,
+    oracle.decode(code.row_ptr, code.col_idx, code.n, llr[idx].astype(np.float64), mu=MU, rho=RHO, eps=eps,
                   max_iter=ITERS, threads=threads)
     dt = time.perf_counter() - t0
     return {"value": n * code.k_design / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{n} of {F} frames (evenly spaced over the 4 Eb/N0 points), {ITERS} iterations each, "
+            "sample": f"{n} of {F} frames (evenly spaced over the 4 Eb/N0 points), "
+                      f"{f'{ITERS} iterations each' if eps == 0 else f'eps={eps:g}, at most {ITERS} iterations'}, "
                       f"FP64, {threads} threads", "seconds": round(dt, 2)}
 
 
@@ -437,7 +441,7 @@ def run_precision(args):
             sample = np.linspace(0, F - 1, 48).astype(int)
             ref = oracle.decode(code.row_ptr, code.col_idx, code.n, llr[sample].astype(np.float64), mu=MU, rho=RHO,
                                 eps=0.0, max_iter=ITERS)
-            for state in ("f32", "bf16", "f16"):
+            for state in ("f32", "bf16", "f16", "q16"):
                 for sched in ("resident", "streamed"):
                     p = lpdec.make_params(mu=MU, rho=RHO, eps=0.0, max_iter=ITERS, state=state, schedule=sched)
                     out = lpdec.decode(C, d_llr, p)
@@ -799,7 +803,7 @@ def main():
     tile = None
     if args.tile:
         gt, g, *ring = (int(v) for v in args.tile.split(","))
-        dt = {"f32": 0, "bf16": 1, "f16": 2}[args.state]
+        dt = {"f32": 0, "bf16": 1, "f16": 2, "q16": 3}[args.state]
         lpdec.lpdec_set_tile(C.handle, dt, gt, g)
         tile = {"group_threads": gt, "groups": g, "source": "--tile"}
         if ring and ring[0]:
@@ -838,8 +842,11 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def time_variant(schedule, state, steps, warmup):
-        p = lpdec.make_params(mu=MU, rho=RHO, eps=0.0, max_iter=ITERS, state=state, schedule=schedule)
+    if args.eps > 0 and args.schedule != "resident":
+        raise SystemExit("--eps > 0 runs the RESIDENT schedule only")
+
+    def time_variant(schedule, state, steps, warmup, eps=0.0):
+        p = lpdec.make_params(mu=MU, rho=RHO, eps=eps, max_iter=ITERS, state=state, schedule=schedule)
         for _ in range(warmup):
             lpdec.decode(C, llr, p, stream=stream, out=out)
         barrier()
@@ -854,22 +861,25 @@ def main():
     # ---- headline: timed region with clock sampling
     sampler = ClockSampler(local)
     with sampler:
-        ms = time_variant(args.schedule, args.state, args.steps, args.warmup)
+        ms = time_variant(args.schedule, args.state, args.steps, args.warmup, args.eps)
     clocks = sampler.summary()
     bits_h = out["bits"].cpu().numpy()
     cert_h = out["cert"].cpu().numpy()
+    # frame-iterations one step runs: all of them at fixed iterations, the
+    # frames' own counts with early exit
+    fi_step = F * ITERS if args.eps == 0 else int(out["iters"].cpu().numpy().astype(np.int64).sum())
     value = ws * F * code.k_design / (ms / 1000.0)
 
     state_bytes = 4 if args.state == "f32" else 2
     B = algorithmic_bytes_per_frame_iter(code, state_bytes)
     launches_per_step = 1 if args.schedule in ("resident", "auto") else ITERS
-    bytes_per_launch = F * (ITERS // launches_per_step) * B
+    bytes_per_launch = fi_step // launches_per_step * B
     launch_ms = ms / launches_per_step
     hbm_peak, peak_kind = measured_peaks()
     achieved = bytes_per_launch / (launch_ms / 1000.0) / 1e9
     kname = f"lpdec::decode_kernel ({code.name}, {args.state}, {args.schedule})"
     if args.schedule == "streamed":
-        ring = lpdec.lpdec_get_tile(C.handle, {"f32": 0, "bf16": 1, "f16": 2}[args.state],
+        ring = lpdec.lpdec_get_tile(C.handle, {"f32": 0, "bf16": 1, "f16": 2, "q16": 3}[args.state],
                                     lpdec.SCHED_STREAMED)["ring_slots"]
         if ring:
             kname = f"lpdec::decode_kernel_ring ({code.name}, {args.state}, streamed, {ring} slots)"
@@ -885,13 +895,13 @@ def main():
             ops, ops_src = rec["fp32_ops"], "counted (ncu instruction counters of this kernel)"
         else:
             ops, ops_src = hand_ops_per_frame_iter(code), "hand count (no counter capture of this kernel)"
-        ach_gops = F * ITERS * ops / (launch_ms / 1000.0) / 1e9
+        ach_gops = fi_step * ops / (launch_ms / 1000.0) / 1e9
         roofline = {
             "bound": "alu", "achieved": round(ach_gops, 1), "peak": round(peak_gops, 1), "unit": "Gop/s",
             "frac": round(ach_gops / peak_gops, 4), "traffic": traffic_per_launch(f"{code.name}/resident/{args.state}", F),
             "kernel": kname,
-            "note": f"{ops} FP32 lane-operations per frame-iteration ({ops_src}; an FMA counts once) x {F} frames x "
-                    f"{ITERS} iterations per launch; peak = 152 SMs x 128 FP32 lanes x {sm_max:.0f} MHz, of measured "
+            "note": f"{ops} FP32 lane-operations per frame-iteration ({ops_src}; an FMA counts once) x {fi_step} "
+                    f"frame-iterations per launch; peak = 152 SMs x 128 FP32 lanes x {sm_max:.0f} MHz, of measured "
                     "maximum SM clock",
             "hbm_effective": {"achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                               "frac": round(achieved / hbm_peak, 4),
@@ -900,7 +910,7 @@ def main():
         }
         if rec:
             peak_wi = 152 * 4 * sm_max * 1e6 / 1e9
-            ach_wi = F * ITERS * rec["warp_inst"] / (launch_ms / 1000.0) / 1e9
+            ach_wi = fi_step * rec["warp_inst"] / (launch_ms / 1000.0) / 1e9
             roofline["issue"] = {"achieved": round(ach_wi, 1), "peak": round(peak_wi, 1), "unit": "G warp-inst/s",
                                  "frac": round(ach_wi / peak_wi, 4),
                                  "note": f"{rec['warp_inst']} warp instructions per frame-iteration (counted) over "
@@ -929,14 +939,16 @@ def main():
         "dtype": args.state, "data": "synthetic",
         "config": {"workload": f"{code.name}: n={code.n} m={code.m} seed {CODE_SEEDS[code.name]}"
                                f"{', 4-cycle free' if code.name in ('C1056', 'C2640') else ''}; {F} frames "
-                               f"({per} at each of 1.5/2.0/2.5/3.0 dB), mu=3 rho=1.9, {ITERS} fixed iterations, "
+                               f"({per} at each of 1.5/2.0/2.5/3.0 dB), mu=3 rho=1.9, "
+                               f"{f'{ITERS} fixed iterations' if args.eps == 0 else f'eps={args.eps:g}, at most {ITERS} iterations'}, "
                                f"FP32 arithmetic, {args.state} edge state (w = z - lambda/mu, lambda/mu)",
                    "schedule": args.schedule, "frames_per_step": F * ws, "tile": tile,
                    "l2": f"inputs larger than L2: {F * code.n * 4 / 1e6:.0f} MB of LLRs read and "
                          f"{F * code.n * 4 / 1e6:.0f} MB of x written per step",
                    "parallelism": f"frames sharded over {ws} rank(s), no collective on the data path"},
         "frames_per_s": ws * F / (ms / 1000.0),
-        "wer": wer, "certified_frac": float(cert_h.mean()),
+        "wer": wer, "certified_frac": float(cert_h.mean()), "mean_iters": fi_step / F,
+        "edge_iterations_per_s": ws * fi_step * code.E / (ms / 1000.0),
         # STREAMED: one decode launch per iteration plus the check for unfinished frames
         "gpu_launches": (launches_per_step + (0 if launches_per_step == 1 else 1)) * args.steps,
         "clocks": clocks,
@@ -945,7 +957,7 @@ def main():
 
     if args.variants and ws == 1:
         var = {}
-        for sch, st in (("streamed", "f32"), ("streamed", "bf16"), ("resident", "bf16")):
+        for sch, st in (("streamed", "f32"), ("streamed", "bf16"), ("streamed", "q16"), ("resident", "bf16")):
             if (sch, st) == (args.schedule, args.state):
                 continue
             vtile = None
@@ -974,7 +986,7 @@ def main():
         b_pin = torch.empty((F, code.n), dtype=torch.uint8).pin_memory()
         i_pin = torch.empty((F,), dtype=torch.int32).pin_memory()
         c_pin = torch.empty((F,), dtype=torch.uint8).pin_memory()
-        p = lpdec.make_params(mu=MU, rho=RHO, eps=0.0, max_iter=ITERS, state=args.state, schedule=args.schedule)
+        p = lpdec.make_params(mu=MU, rho=RHO, eps=args.eps, max_iter=ITERS, state=args.state, schedule=args.schedule)
         sp = int(stream.cuda_stream)
 
         def host_step():
@@ -994,7 +1006,7 @@ def main():
                        "ms_per_step": 1000 * e2e_s}
 
     if rank == 0:
-        line["cpu_baseline"] = oracle_sample(code, llr_h, args.cpu_seconds)
+        line["cpu_baseline"] = oracle_sample(code, llr_h, args.cpu_seconds, args.eps)
         print(json.dumps(line), flush=True)
     C.close()
     if ws > 1:

@@ -70,6 +70,11 @@ extern "C" {
 #define LPDEC_STATE_F32  0
 #define LPDEC_STATE_BF16 1 /* round-to-nearest-even on every store; FP32 arithmetic */
 #define LPDEC_STATE_F16  2 /* round-to-nearest-even on every store; FP32 arithmetic */
+#define LPDEC_STATE_Q16  3 /* 16-bit fixed point: k * s with k a 16-bit integer and s the smallest
+                              power of two with 32767 s >= 1 + 6/mu (2^-13 at mu = 3), rounded to
+                              nearest on every store; values beyond +-32767 s saturate.  FP32
+                              arithmetic.  Uniform absolute precision: w and lambda/mu live in a
+                              range of a few units, where BF16/FP16 lose low bits to the exponent. */
 
 /* ---- schedules --------------------------------------------------------- */
 #define LPDEC_SCHED_AUTO     0 /* RESIDENT when a frame's state fits in shared memory, else STREAMED */

@@ -554,7 +554,7 @@ int validate_params(const lpdec_params *p) {
     if (!(p->rho >= 1.0 && p->rho < 2.0)) return set_error(LPDEC_EINVAL, "rho=%g must be in [1, 2)", p->rho);
     if (!(p->eps >= 0.0) || !std::isfinite(p->eps)) return set_error(LPDEC_EINVAL, "eps=%g must be >= 0", p->eps);
     if (p->max_iter < 1) return set_error(LPDEC_EINVAL, "max_iter=%d must be >= 1", p->max_iter);
-    if (p->state_dtype < 0 || p->state_dtype > 2) return set_error(LPDEC_EINVAL, "unknown state_dtype %d", p->state_dtype);
+    if (p->state_dtype < 0 || p->state_dtype > 3) return set_error(LPDEC_EINVAL, "unknown state_dtype %d", p->state_dtype);
     if (!(p->cert_tol > 0.0 && p->cert_tol < 0.5)) return set_error(LPDEC_EINVAL, "cert_tol=%g must be in (0, 0.5)", p->cert_tol);
     if (p->schedule < 0 || p->schedule > 2) return set_error(LPDEC_EINVAL, "unknown schedule %d", p->schedule);
     if (p->iters_per_launch < 1) return set_error(LPDEC_EINVAL, "iters_per_launch=%d must be >= 1", p->iters_per_launch);
@@ -567,6 +567,7 @@ IterCfg make_cfg(const lpdec_code *c, const lpdec_params *p) {
     IterCfg cfg;
     cfg.mu_inv = (float)(1.0 / p->mu);
     cfg.rho = (float)p->rho;
+    cfg.rho_inv = (float)(1.0 / p->rho);
     cfg.omr = (float)(1.0 - p->rho);
     cfg.tmr = (float)(2.0 - p->rho);
     cfg.cert_tol = (float)p->cert_tol;
@@ -575,6 +576,14 @@ IterCfg make_cfg(const lpdec_code *c, const lpdec_params *p) {
     cfg.epsc2E = epsc * epsc * (double)c->E;
     cfg.max_iter = p->max_iter;
     cfg.check_stop = p->eps > 0.0 ? 1 : 0;
+    // Q16 state: the smallest power of two s with 32767 s >= 1 + 6/mu, a bound on
+    // |w| = |z - lambda/mu| and |lambda/mu| (|lambda| stayed below 5.5 in FP64
+    // runs of the benchmark codes from 0 to 9 dB); mu = 3 gives s = 2^-13.
+    const double bound = 1.0 + 6.0 / p->mu;
+    const int e = (int)std::ceil(std::log2(bound / 32767.0));
+    cfg.q.s = (float)std::ldexp(1.0, e);
+    cfg.q.inv = (float)std::ldexp(1.0, -e);
+    cfg.q.off = -12615680.0f * cfg.q.s;
     return cfg;
 }
 
@@ -927,7 +936,7 @@ extern "C" int lpdec_autotune(lpdec_code *c, const lpdec_params *p, int32_t n_fr
 
 extern "C" int lpdec_set_tile(lpdec_code *c, int32_t state_dtype, int32_t group_threads, int32_t groups) {
     if (!c) return set_error(LPDEC_EINVAL, "lpdec_set_tile: code is NULL");
-    if (state_dtype < 0 || state_dtype > 2) return set_error(LPDEC_EINVAL, "lpdec_set_tile: unknown state_dtype");
+    if (state_dtype < 0 || state_dtype > 3) return set_error(LPDEC_EINVAL, "lpdec_set_tile: unknown state_dtype");
     if (group_threads == 0 && groups == 0) {  // back to the built-in default
         c->tuned[state_dtype] = lpdec::Tile();
         c->tuned_streamed[state_dtype] = lpdec::Tile();
@@ -952,7 +961,7 @@ extern "C" int lpdec_set_tile(lpdec_code *c, int32_t state_dtype, int32_t group_
 extern "C" int lpdec_set_streamed_tile(lpdec_code *c, int32_t state_dtype, int32_t group_threads, int32_t groups,
                                        int32_t ring_slots) {
     if (!c) return set_error(LPDEC_EINVAL, "lpdec_set_streamed_tile: code is NULL");
-    if (state_dtype < 0 || state_dtype > 2) return set_error(LPDEC_EINVAL, "lpdec_set_streamed_tile: unknown state_dtype");
+    if (state_dtype < 0 || state_dtype > 3) return set_error(LPDEC_EINVAL, "lpdec_set_streamed_tile: unknown state_dtype");
     if (group_threads == 0 && groups == 0 && ring_slots == 0) {
         c->tuned_streamed[state_dtype] = lpdec::Tile();
         return LPDEC_OK;
@@ -988,7 +997,7 @@ extern "C" int lpdec_set_streamed_tile(lpdec_code *c, int32_t state_dtype, int32
 extern "C" int lpdec_get_tile(const lpdec_code *c, int32_t state_dtype, int32_t schedule, int32_t *group_threads,
                               int32_t *groups, int32_t *ring_slots) {
     if (!c) return set_error(LPDEC_EINVAL, "lpdec_get_tile: code is NULL");
-    if (state_dtype < 0 || state_dtype > 2) return set_error(LPDEC_EINVAL, "lpdec_get_tile: unknown state_dtype");
+    if (state_dtype < 0 || state_dtype > 3) return set_error(LPDEC_EINVAL, "lpdec_get_tile: unknown state_dtype");
     if (schedule < 0 || schedule > 2) return set_error(LPDEC_EINVAL, "lpdec_get_tile: unknown schedule");
     lpdec_params p;
     lpdec_params_default(&p);

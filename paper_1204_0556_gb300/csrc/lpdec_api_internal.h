@@ -67,7 +67,7 @@ struct lpdec_code {
     // Regular codes: 16-bit index block (CodeView::col16 / csc16), else null.
     void *dev_idx16 = nullptr;
     int idx16_bytes = 0, col16_elems = 0;
-    lpdec::Tile tuned[3];           // per state dtype, from lpdec_autotune (RESIDENT) or lpdec_set_tile
-    lpdec::Tile tuned_streamed[3];  // per state dtype, from lpdec_autotune (STREAMED) or lpdec_set_tile
+    lpdec::Tile tuned[4];           // per state dtype, from lpdec_autotune (RESIDENT) or lpdec_set_tile
+    lpdec::Tile tuned_streamed[4];  // per state dtype, from lpdec_autotune (STREAMED) or lpdec_set_tile
     lpdec::Tile dual_tile;  // tile of the dual subgradient decoder, from lpdec_dual_set_tile
 };

@@ -48,34 +48,88 @@ constexpr float kBigKappa = 1.0e30f;
 
 // ---------------------------------------------------------------------------
 // storage conversions
-template <typename S> __device__ __forceinline__ float ld(S v);
-template <> __device__ __forceinline__ float ld<float>(float v) { return v; }
-template <> __device__ __forceinline__ float ld<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
-template <> __device__ __forceinline__ float ld<__half>(__half v) { return __half2float(v); }
+//
+// q16_t: 16-bit fixed point.  A stored value is k * s with k a signed 16-bit
+// integer kept biased (b = k + 32768) and s = 2^e a per-decode power of two
+// (QScale, chosen on the host from mu).  With b in the low half of a word
+// whose high half is 0x4B40, the word is the float 1.5 * 2^23 + b exactly, so
+// a load is one byte permute and one FFMA, (f - (1.5 * 2^23 + 32768)) * s,
+// exact; a store is one FFMA, v / s + 1.5 * 2^23 + 32768 rounded to the
+// nearest integer by the addition, clamped to the 16-bit range (values beyond
+// +-32767 s saturate), whose low half is b.
+struct q16_t {
+    uint16_t b;
+};
+struct QScale {
+    float s;    // 2^e
+    float off;  // -(1.5 * 2^23 + 32768) * s
+    float inv;  // 1 / s
+};
+constexpr float kQMagic = 12615680.0f;  // 1.5 * 2^23 + 32768
+constexpr float kQLo = 12582912.0f;     // b = 0
+constexpr float kQHi = 12648447.0f;     // b = 65535
 
-template <typename S> __device__ __forceinline__ S st(float v);
-template <> __device__ __forceinline__ float st<float>(float v) { return v; }
-template <> __device__ __forceinline__ __nv_bfloat16 st<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
-template <> __device__ __forceinline__ __half st<__half>(float v) { return __float2half_rn(v); }
+__device__ __forceinline__ float q16_decode(unsigned word, unsigned sel, const QScale &q) {
+    return fmaf(__int_as_float((int)__byte_perm(word, 0x4B400000u, sel)), q.s, q.off);
+}
+__device__ __forceinline__ unsigned q16_encode(float v, const QScale &q) {
+    return (unsigned)__float_as_int(fminf(fmaxf(fmaf(v, q.inv, kQMagic), kQLo), kQHi));
+}
+
+template <typename S> __device__ __forceinline__ float ld(S v, const QScale &q);
+template <> __device__ __forceinline__ float ld<float>(float v, const QScale &) { return v; }
+template <> __device__ __forceinline__ float ld<__nv_bfloat16>(__nv_bfloat16 v, const QScale &) {
+    return __bfloat162float(v);
+}
+template <> __device__ __forceinline__ float ld<__half>(__half v, const QScale &) { return __half2float(v); }
+template <> __device__ __forceinline__ float ld<q16_t>(q16_t v, const QScale &q) { return q16_decode(v.b, 0x7610, q); }
+
+template <typename S> __device__ __forceinline__ S st(float v, const QScale &q);
+template <> __device__ __forceinline__ float st<float>(float v, const QScale &) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 st<__nv_bfloat16>(float v, const QScale &) {
+    return __float2bfloat16_rn(v);
+}
+template <> __device__ __forceinline__ __half st<__half>(float v, const QScale &) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ q16_t st<q16_t>(float v, const QScale &q) {
+    q16_t r;
+    r.b = (uint16_t)(q16_encode(v, q) & 0xffffu);
+    return r;
+}
 
 // Two adjacent state elements (for even-aligned pairs of edges of a check).
-template <typename S> __device__ __forceinline__ float2 ld2(const S *p);
-template <> __device__ __forceinline__ float2 ld2<float>(const float *p) { return *reinterpret_cast<const float2 *>(p); }
-template <> __device__ __forceinline__ float2 ld2<__half>(const __half *p) {
+template <typename S> __device__ __forceinline__ float2 ld2(const S *p, const QScale &q);
+template <> __device__ __forceinline__ float2 ld2<float>(const float *p, const QScale &) {
+    return *reinterpret_cast<const float2 *>(p);
+}
+template <> __device__ __forceinline__ float2 ld2<__half>(const __half *p, const QScale &) {
     return __half22float2(*reinterpret_cast<const __half2 *>(p));
 }
-template <> __device__ __forceinline__ float2 ld2<__nv_bfloat16>(const __nv_bfloat16 *p) {
+template <> __device__ __forceinline__ float2 ld2<__nv_bfloat16>(const __nv_bfloat16 *p, const QScale &) {
     return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
 }
-template <typename S> __device__ __forceinline__ void st2(S *p, float a, float b);
-template <> __device__ __forceinline__ void st2<float>(float *p, float a, float b) {
+template <> __device__ __forceinline__ float2 ld2<q16_t>(const q16_t *p, const QScale &q) {
+    const unsigned w = *reinterpret_cast<const unsigned *>(p);
+    const float2 f = make_float2(__int_as_float((int)__byte_perm(w, 0x4B400000u, 0x7610)),
+                                 __int_as_float((int)__byte_perm(w, 0x4B400000u, 0x7632)));
+    return __ffma2_rn(f, make_float2(q.s, q.s), make_float2(q.off, q.off));  // each lane exact, as q16_decode
+}
+template <typename S> __device__ __forceinline__ void st2(S *p, float a, float b, const QScale &q);
+template <> __device__ __forceinline__ void st2<float>(float *p, float a, float b, const QScale &) {
     *reinterpret_cast<float2 *>(p) = make_float2(a, b);
 }
-template <> __device__ __forceinline__ void st2<__half>(__half *p, float a, float b) {
+template <> __device__ __forceinline__ void st2<__half>(__half *p, float a, float b, const QScale &) {
     *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a, b);
 }
-template <> __device__ __forceinline__ void st2<__nv_bfloat16>(__nv_bfloat16 *p, float a, float b) {
+template <> __device__ __forceinline__ void st2<__nv_bfloat16>(__nv_bfloat16 *p, float a, float b, const QScale &) {
     *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
+}
+template <> __device__ __forceinline__ void st2<q16_t>(q16_t *p, float a, float b, const QScale &q) {
+    *reinterpret_cast<unsigned *>(p) = __byte_perm(q16_encode(a, q), q16_encode(b, q), 0x5410);
+}
+
+// Bit pattern of two stored zeros (the initial z = lambda = 0).
+template <typename S> __host__ __device__ constexpr unsigned state_zero2() {
+    return std::is_same<S, q16_t>::value ? 0x80008000u : 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -255,6 +309,7 @@ struct CodeView {
 struct IterCfg {
     float mu_inv;       // 1/mu
     float rho;          // over-relaxation
+    float rho_inv;      // 1/rho
     float omr;          // 1 - rho
     float tmr;          // 2 - rho
     float cert_tol;
@@ -262,6 +317,7 @@ struct IterCfg {
     double epsc2E;      // max(eps, 1e-5)^2 * E
     int max_iter;
     int check_stop;     // eps > 0
+    QScale q;           // q16_t state only: the fixed-point scale
 };
 
 struct DecodeArgs {
@@ -343,8 +399,8 @@ __device__ __forceinline__ void check_update(const CodeView &c, const IterCfg &p
         const uint32_t *ci = reinterpret_cast<const uint32_t *>(c.col16 + e0);
 #pragma unroll
         for (int k = 0; k < D; k += 2) {
-            const float2 w2 = ld2<S>(ws + e0 + k);  // u = rho x + (1 - rho) w when folded
-            const float2 l2 = ld2<S>(ls + e0 + k);
+            const float2 w2 = ld2<S>(ws + e0 + k, p.q);  // u = rho x + (1 - rho) w when folded
+            const float2 l2 = ld2<S>(ls + e0 + k, p.q);
             if constexpr (!RES && kFoldX<S>) {  // regular form (kPairs): ws holds u
                 const float2 vv = __ffma2_rn(make_float2(p.tmr, p.tmr), l2, w2);  // packed pair, lane = fmaf
                 v[k] = vv.x;
@@ -368,15 +424,15 @@ __device__ __forceinline__ void check_update(const CodeView &c, const IterCfg &p
         for (int k = 0; k < D; ++k) {
             if (k < d) {
                 const int e = e0 + k;
-                const float lk = ld<S>(ls[e]);
+                const float lk = ld<S>(ls[e], p.q);
                 const float xk = xs[__ldg(c.col_idx + e)];
                 if constexpr (RES) {
-                    const float zk = ld<S>(ws[e]) + lk;  // z_j^old
+                    const float zk = ld<S>(ws[e], p.q) + lk;  // z_j^old
                     if constexpr (kKeep) { xv[k] = xk; zo[k] = zk; }
                     const float q = fmaf(p.rho, xk, p.omr * zk);  // rho P_j x + (1 - rho) z_j^old
                     v[k] = q + lk;                                 // v_j = q + lambda_j / mu
                 } else {
-                    v[k] = fmaf(p.rho, xk, fmaf(p.omr, ld<S>(ws[e]), p.tmr * lk));
+                    v[k] = fmaf(p.rho, xk, fmaf(p.omr, ld<S>(ws[e], p.q), p.tmr * lk));
                 }
             } else {
                 v[k] = kPadV;
@@ -394,8 +450,8 @@ __device__ __forceinline__ void check_update(const CodeView &c, const IterCfg &p
             const float2 zz = make_float2(z0, z1);
             const float2 ll = __ffma2_rn(zz, m1, make_float2(v[k], v[k + 1]));
             const float2 ww = __ffma2_rn(ll, m1, zz);
-            st2<S>(ls + e0 + k, ll.x, ll.y);
-            st2<S>(ws + e0 + k, ww.x, ww.y);
+            st2<S>(ls + e0 + k, ll.x, ll.y, p.q);
+            st2<S>(ws + e0 + k, ww.x, ww.y, p.q);
             if constexpr (RES) {
                 float a = xv[k] - z0, b = z0 - zo[k];
                 rp = fmaf(a, a, rp);
@@ -414,10 +470,10 @@ __device__ __forceinline__ void check_update(const CodeView &c, const IterCfg &p
                 const float z = proj_z(v[k], pr, k);
                 float xk = 0.0f, zk = 0.0f;
                 if constexpr (kKeep) { xk = xv[k]; zk = zo[k]; }
-                else if constexpr (RES) { xk = xs[__ldg(c.col_idx + e)]; zk = ld<S>(ws[e]) + ld<S>(ls[e]); }
+                else if constexpr (RES) { xk = xs[__ldg(c.col_idx + e)]; zk = ld<S>(ws[e], p.q) + ld<S>(ls[e], p.q); }
                 const float l = v[k] - z;  // lambda/mu += q - z, i.e. lambda/mu = v - z
-                ls[e] = st<S>(l);
-                ws[e] = st<S>(z - l);
+                ls[e] = st<S>(l, p.q);
+                ws[e] = st<S>(z - l, p.q);
                 if constexpr (RES) {
                     const float a = xk - z;
                     const float b = z - zk;
@@ -585,10 +641,10 @@ __device__ __forceinline__ void check_update_w(const CodeView &c, const IterCfg 
     for (int k = 0; k < V; ++k) {
         if (k * L < dr) {
             if constexpr (kFold) {
-                kap[k] = fmaf(p.tmr, ld<S>(lsj[k * L]), ld<S>(wsj[k * L]));
+                kap[k] = fmaf(p.tmr, ld<S>(lsj[k * L], p.q), ld<S>(wsj[k * L], p.q));
             } else {
                 const float xk = xs[col_of(eb + k * L)];
-                kap[k] = fmaf(p.rho, xk, fmaf(p.omr, ld<S>(wsj[k * L]), p.tmr * ld<S>(lsj[k * L])));
+                kap[k] = fmaf(p.rho, xk, fmaf(p.omr, ld<S>(wsj[k * L], p.q), p.tmr * ld<S>(lsj[k * L], p.q)));
             }
         } else {
             kap[k] = kPadV;
@@ -606,13 +662,17 @@ __device__ __forceinline__ void check_update_w(const CodeView &c, const IterCfg 
             const float w = z - l;
             const int e = eb + k * L;
             if constexpr (RES) {
-                const float a = xs[col_of(e)] - z;
-                const float b = z - (ld<S>(ws[e]) + ld<S>(ls[e]));
+                // x_i(e) from v = rho x + (1 - rho) w_old + (2 - rho) lambda_old/mu
+                // rather than a second gather (equal up to FP32 rounding)
+                const float wo = ld<S>(ws[e], p.q), lo = ld<S>(ls[e], p.q);
+                const float xk = (v - fmaf(p.omr, wo, p.tmr * lo)) * p.rho_inv;
+                const float a = xk - z;
+                const float b = z - (wo + lo);
                 rp = fmaf(a, a, rp);
                 rd = fmaf(b, b, rd);
             }
-            ls[e] = st<S>(l);
-            ws[e] = st<S>(w);
+            ls[e] = st<S>(l, p.q);
+            ws[e] = st<S>(w, p.q);
         }
     }
 }
@@ -638,11 +698,13 @@ __device__ __forceinline__ void copy16(void *dst, const void *src, int nbytes, i
     const uint4 *s = reinterpret_cast<const uint4 *>(src);
     for (int i = t; i < (nbytes >> 4); i += T) d[i] = s[i];
 }
-__device__ __forceinline__ void zero16(void *dst, int nbytes, int t, int T) {
+// Fill nbytes (a multiple of 16) with a repeated 32-bit pattern, cooperatively.
+__device__ __forceinline__ void fill16(void *dst, int nbytes, unsigned pattern, int t, int T) {
     uint4 *d = reinterpret_cast<uint4 *>(dst);
-    const uint4 zz = make_uint4(0u, 0u, 0u, 0u);
+    const uint4 zz = make_uint4(pattern, pattern, pattern, pattern);
     for (int i = t; i < (nbytes >> 4); i += T) d[i] = zz;
 }
+__device__ __forceinline__ void zero16(void *dst, int nbytes, int t, int T) { fill16(dst, nbytes, 0u, t, T); }
 
 // ---------------------------------------------------------------------------
 // Bulk asynchronous copies (TMA engine, non-tensor form) between global and
@@ -733,7 +795,9 @@ struct FrameIO {
 // Returns false only if a bulk copy timed out; the group must then stop.
 // READY (STREAMED ring): a parked frame's state is already in sm (the caller
 // waited for its copies), so no copy is issued or awaited here.
-template <int D, int L, int DV, typename S, bool READY = false>
+// PF (regular form with the 16-bit indices in global memory): the x-update
+// loads the next variable's edge ids and LLR while it processes this one.
+template <int D, int L, int DV, typename S, bool READY = false, bool PF = false>
 __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, int iters_this_launch, const FrameIO &io,
                           const Slice<S> &sm, int t, int T, int bar, uint32_t &phase) {
     const int lane = t & 31, w = t >> 5, nw = T >> 5;
@@ -751,7 +815,7 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
         // Algorithm 1 initialization: z = lambda = 0 (w = 0).  Also reject non-finite LLRs.
         int bad = 0;
         for (int i = t; i < c.n; i += T) bad |= !isfinite(llr_at<READY>(gam, gam_s, i));
-        zero16(sm.w, 2 * state_bytes, t, T);
+        fill16(sm.w, 2 * state_bytes, state_zero2<S>(), t, T);
         bad = __any_sync(0xffffffffu, bad);
         group_sync(bar, T);
         if (bad && lane == 0) atomicOr((int *)&flags[2], 1);
@@ -806,20 +870,39 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
         // generic form would need a second pass over each variable's edges.)
         const bool fold = kFoldX<S> && DV > 0 && !need_res;
         // ---- x-update (Algorithm 1; Section 3.2): sum over the edges of w = z - lambda/mu
+        uint2 pk_next = make_uint2(0u, 0u);
+        float g_next = 0.0f;
+        if constexpr (DV > 0 && PF) {
+            if (t < c.n) {
+                pk_next = *reinterpret_cast<const uint2 *>(c.csc16 + 4 * t);
+                g_next = llr_at<READY>(gam, gam_s, t);
+            }
+        }
         for (int i = t; i < c.n; i += T) {
             float acc = 0.0f, inv_dv;
             if constexpr (DV > 0) {
                 static_assert(DV <= 4, "regular form holds up to 4 edges per variable");
-                const uint2 pk = *reinterpret_cast<const uint2 *>(c.csc16 + 4 * i);
+                uint2 pk;
+                float gi;
+                if constexpr (PF) {
+                    pk = pk_next;
+                    gi = g_next;
+                    if (i + T < c.n) {
+                        pk_next = *reinterpret_cast<const uint2 *>(c.csc16 + 4 * (i + T));
+                        g_next = llr_at<READY>(gam, gam_s, i + T);
+                    }
+                } else {
+                    pk = *reinterpret_cast<const uint2 *>(c.csc16 + 4 * i);
+                    gi = llr_at<READY>(gam, gam_s, i);
+                }
                 const unsigned es[4] = {pk.x & 0xffffu, pk.x >> 16, pk.y & 0xffffu, pk.y >> 16};
                 float wv[DV];
 #pragma unroll
                 for (int s = 0; s < DV; ++s) {
-                    wv[s] = ld<S>(sm.w[es[s]]);
+                    wv[s] = ld<S>(sm.w[es[s]], p.q);
                     acc += wv[s];
                 }
                 inv_dv = 1.0f / (float)DV;
-                const float gi = llr_at<READY>(gam, gam_s, i);
                 const float x = __saturatef((acc - gi * p.mu_inv) * inv_dv);
                 sm.x[i] = x;
                 if (fold) {
@@ -828,16 +911,16 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
                     for (int s = 0; s + 1 < DV; s += 2) {  // packed FP32 pairs (each lane rounds as fmaf)
                         const float2 uu = __ffma2_rn(make_float2(p.omr, p.omr), make_float2(wv[s], wv[s + 1]),
                                                      make_float2(rx, rx));
-                        sm.w[es[s]] = st<S>(uu.x);
-                        sm.w[es[s + 1]] = st<S>(uu.y);
+                        sm.w[es[s]] = st<S>(uu.x, p.q);
+                        sm.w[es[s + 1]] = st<S>(uu.y, p.q);
                     }
-                    if (DV & 1) sm.w[es[DV - 1]] = st<S>(fmaf(p.omr, wv[DV - 1], rx));
+                    if (DV & 1) sm.w[es[DV - 1]] = st<S>(fmaf(p.omr, wv[DV - 1], rx), p.q);
                 }
             } else {
                 const int s0 = __ldg(c.col_ptr + i), s1 = __ldg(c.col_ptr + i + 1);
                 for (int s = s0; s < s1; ++s) {
                     const int e = __ldg(c.csc_edge + s);
-                    acc += ld<S>(sm.w[e]);
+                    acc += ld<S>(sm.w[e], p.q);
                 }
                 inv_dv = __frcp_rn((float)(s1 - s0));
                 const float gi = llr_at<READY>(gam, gam_s, i);
@@ -877,11 +960,18 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
             rd = warp_sum(rd);
             if (lane == 0) { sm.red[2 * w] = rp; sm.red[2 * w + 1] = rd; }
             group_sync(bar, T);
-            if (t == 0) {
-                double Rp = 0.0, Rd = 0.0;
-                for (int q = 0; q < nw; ++q) { Rp += (double)sm.red[2 * q]; Rd += (double)sm.red[2 * q + 1]; }
-                flags[0] = (p.check_stop && Rp < p.eps2E && Rd < p.eps2E) ? 1 : 0;
-                flags[1] = (Rp < p.epsc2E && Rd < p.epsc2E) ? 1 : 0;
+            if (w == 0) {
+                // the warps' partial sums added in FP64 across the lanes of warp 0
+                double Rp = lane < nw ? (double)sm.red[2 * lane] : 0.0;
+                double Rd = lane < nw ? (double)sm.red[2 * lane + 1] : 0.0;
+                for (int o = 1; o < nw; o <<= 1) {
+                    Rp += __shfl_xor_sync(0xffffffffu, Rp, o);
+                    Rd += __shfl_xor_sync(0xffffffffu, Rd, o);
+                }
+                if (lane == 0) {
+                    flags[0] = (p.check_stop && Rp < p.eps2E && Rd < p.eps2E) ? 1 : 0;
+                    flags[1] = (Rp < p.epsc2E && Rd < p.epsc2E) ? 1 : 0;
+                }
             }
             group_sync(bar, T);
             conv = flags[0] != 0;
@@ -1011,7 +1101,7 @@ __global__ void __launch_bounds__(MAXT, 1) decode_kernel(const DecodeArgs a) {
         if (q >= a.n_frames) break;
         const int f = a.frame_list ? a.frame_list[q] : q;
         const FrameIO io = frame_io<S>(a, f);
-        if (!frame_run<D, L, DV, S>(cv, a.cfg, a.iters_this_launch, io, sm, t, T, bar, phase)) break;
+        if (!frame_run<D, L, DV, S, false, !STAGE>(cv, a.cfg, a.iters_this_launch, io, sm, t, T, bar, phase)) break;
     }
     if (t == 0) bulk_wait_all();
 }
@@ -1223,7 +1313,7 @@ __global__ void __launch_bounds__(MAXT, 1) decode_kernel_ring(const DecodeArgs a
         sm.llr = a.ring_llr_off ? reinterpret_cast<const float *>(reinterpret_cast<const char *>(sm.w) + a.ring_llr_off)
                                 : nullptr;
         const FrameIO io = frame_io<S>(a, f);
-        frame_run<D, L, DV, S, true>(cv, a.cfg, a.iters_this_launch, io, sm, t, T, bar, unused_phase);
+        frame_run<D, L, DV, S, true, !STAGE>(cv, a.cfg, a.iters_this_launch, io, sm, t, T, bar, unused_phase);
         if (t == 0) {
             // the group's writes to the slot (ordered by its last barrier) and
             // the parking copies' reads of it are done before the producer

@@ -40,6 +40,7 @@ const void *decode_fn_dtype(int dtype) {
         case 0: return decode_fn<DV, STAGE, RING, float>();
         case 1: return decode_fn<DV, STAGE, RING, __nv_bfloat16>();
         case 2: return decode_fn<DV, STAGE, RING, __half>();
+        case 3: return decode_fn<DV, STAGE, RING, q16_t>();
         default: return nullptr;
     }
 }
@@ -72,6 +73,7 @@ cudaError_t launch_dv(int dtype, const DecodeArgs &a, const LaunchCfg &lc) {
         case 0: launch_one<DV, STAGE, RING, float>(a, lc); break;
         case 1: launch_one<DV, STAGE, RING, __nv_bfloat16>(a, lc); break;
         case 2: launch_one<DV, STAGE, RING, __half>(a, lc); break;
+        case 3: launch_one<DV, STAGE, RING, q16_t>(a, lc); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -82,7 +84,7 @@ cudaError_t launch_dv(int dtype, const DecodeArgs &a, const LaunchCfg &lc) {
 // ([dtype][form]); the attribute is set only when a launch needs more, so
 // decodes in a steady state (and under CUDA-graph capture) make no attribute
 // calls.  Per device: a kernel attribute is per device.
-static std::atomic<int> g_smem_granted[64][3][kForms];
+static std::atomic<int> g_smem_granted[64][4][kForms];
 
 cudaError_t LPDEC_CAT(prepare_decode_, LPDEC_D)(int dtype, int reg_dv, bool stage, bool ring, size_t smem) {
     const int form = form_of(reg_dv, stage, ring);

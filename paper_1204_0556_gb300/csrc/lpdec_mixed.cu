@@ -35,21 +35,24 @@ struct MixedIO {
 // One group's share of a round: pull frames of the current code until its
 // queue is empty.  Two kernels use it.  The FAST kernel inlines the three most
 // common forms ((3,6), (4,8), and checks of degree 21..32 with degree-3
-// variables) and serves batches whose codes all take one of them.  The general
+// variables) and serves batches whose codes each take one of them, each form
+// at most once; the host then puts the code of form s in slot s, so the
+// kernel names its descriptor by a constant index and the descriptor's fields
+// are read from the kernel's parameter space at fixed offsets.  The general
 // kernel calls every form through mixed_round_call, not inlined, so that each
-// gets the whole register budget: inlining five forms spilled 232 B, three
-// spill 64 B, and a kernel that mixes inlined forms with calls loses the gain
-// (the FAST kernel runs the C1056/C2640/C4000 batch 5.6 % faster than calls).
+// gets the whole register budget (inlining five forms spilled 232 B), with
+// the descriptor of the current code copied to shared memory.
 template <int D, int L, int DV, typename S>
-__device__ __forceinline__ void mixed_round(const MixedCode *mc, MixedIO b, unsigned char *smem_raw, int g, int t) {
-    const int T = mc->group_threads;
+__device__ __forceinline__ void mixed_round(const MixedCode &mc, const CodeView &cv, MixedIO b,
+                                            unsigned char *smem_raw, int g, int t) {
+    const int T = mc.group_threads;
     const int bar = 1 + g;
-    unsigned char *base = smem_raw + (size_t)g * mc->smem_per_group;
+    unsigned char *base = smem_raw + (size_t)g * mc.smem_per_group;
     Slice<S> sm;
     sm.w = reinterpret_cast<S *>(base);
-    sm.l = sm.w + mc->view.Ep;
-    sm.x = reinterpret_cast<float *>(base + mc->off_x);
-    sm.red = reinterpret_cast<float *>(base + mc->off_red);
+    sm.l = sm.w + cv.Ep;
+    sm.x = reinterpret_cast<float *>(base + mc.off_x);
+    sm.red = reinterpret_cast<float *>(base + mc.off_red);
     sm.flags = reinterpret_cast<int *>(sm.red + 2 * (T >> 5));
     sm.mbar = reinterpret_cast<uint64_t *>(sm.flags + 6);
     uint32_t phase = 0;
@@ -59,8 +62,8 @@ __device__ __forceinline__ void mixed_round(const MixedCode *mc, MixedIO b, unsi
         group_sync(bar, T);
         const int idx = sm.flags[4 + par];
         par ^= 1;
-        if (idx >= mc->n_frames) break;
-        const int f = mc->frames[idx];
+        if (idx >= mc.n_frames) break;
+        const int f = mc.frames[idx];
         const size_t off = (size_t)b.offset[f];
         FrameIO io;
         io.llr = b.llr + off;
@@ -70,13 +73,26 @@ __device__ __forceinline__ void mixed_round(const MixedCode *mc, MixedIO b, unsi
         io.cert = b.cert_out ? b.cert_out + f : nullptr;
         io.w_state = io.l_state = nullptr;
         io.k_state = nullptr;
-        frame_run<D, L, DV, S>(mc->view, mc->cfg, mc->cfg.max_iter, io, sm, t, T, bar, phase);
+        frame_run<D, L, DV, S>(cv, mc.cfg, mc.cfg.max_iter, io, sm, t, T, bar, phase);
     }
 }
 
+// General kernel: the descriptor (with its staged index pointers) is in shared memory.
 template <int D, int L, int DV, typename S>
 __device__ __noinline__ void mixed_round_call(const MixedCode *mc, MixedIO b, unsigned char *smem_raw, int g, int t) {
-    mixed_round<D, L, DV, S>(mc, b, smem_raw, g, t);
+    mixed_round<D, L, DV, S>(*mc, mc->view, b, smem_raw, g, t);
+}
+
+// FAST kernel: mc is a descriptor of the kernel's parameter block; only the
+// staged index pointers are rebuilt here.
+template <int D, int L, int DV, typename S>
+__device__ __forceinline__ void fast_round(const MixedCode &mc, MixedIO b, unsigned char *smem_raw, int g, int t) {
+    CodeView cv = mc.view;
+    if (mc.idx_off >= 0) {
+        cv.col16 = reinterpret_cast<const uint16_t *>(smem_raw + mc.idx_off);
+        cv.csc16 = cv.col16 + mc.view.col16_elems;
+    }
+    mixed_round<D, L, DV, S>(mc, cv, b, smem_raw, g, t);
 }
 
 template <typename S, bool FAST>
@@ -107,10 +123,10 @@ __global__ void __launch_bounds__(kMixedMaxThreads, 1) mixed_kernel(const MixedA
             MixedIO b{a.offset, a.llr, a.x_out, a.bits_out, a.iters_out, a.cert_out, a.queues + cur};
             const int t = threadIdx.x - g * T;
             if constexpr (FAST) {
-                switch (cur_code.kind) {
-                    case kK6R3: mixed_round<6, 1, 3, S>(&cur_code, b, smem_raw, g, t); break;
-                    case kK8R4: mixed_round<8, 1, 4, S>(&cur_code, b, smem_raw, g, t); break;
-                    default: mixed_round<32, class_lanes(32), 3, S>(&cur_code, b, smem_raw, g, t); break;  // kK32R3
+                switch (cur) {  // slot s holds the code of FAST form s
+                    case 0: fast_round<6, 1, 3, S>(a.code[0], b, smem_raw, g, t); break;
+                    case 1: fast_round<8, 1, 4, S>(a.code[1], b, smem_raw, g, t); break;
+                    default: fast_round<32, class_lanes(32), 3, S>(a.code[2], b, smem_raw, g, t); break;
                 }
             } else {
                 switch (cur_code.kind) {
@@ -152,6 +168,7 @@ const void *mixed_fn_t(int dtype) {
         case 0: return reinterpret_cast<const void *>(&mixed_kernel<float, FAST>);
         case 1: return reinterpret_cast<const void *>(&mixed_kernel<__nv_bfloat16, FAST>);
         case 2: return reinterpret_cast<const void *>(&mixed_kernel<__half, FAST>);
+        case 3: return reinterpret_cast<const void *>(&mixed_kernel<q16_t, FAST>);
         default: return nullptr;
     }
 }
@@ -202,6 +219,34 @@ int mixed_setup(const char *who, const lpdec_code *const *codes, int32_t n_codes
     const int dev = codes[0]->device;
     for (int c = 1; c < n_codes; ++c)
         if (codes[c]->device != dev) return set_error(LPDEC_EINVAL, "%s: codes on different devices", who);
+    for (int f = 0; f < n_frames; ++f)
+        if (frame_code[f] < 0 || frame_code[f] >= n_codes)
+            return set_error(LPDEC_EINVAL, "%s: frame_code[%d]=%d out of range", who, f, frame_code[f]);
+
+    // FAST batches: every code takes one of the FAST kernel's three forms, each
+    // form at most once.  The codes then move to the slot of their form (a form
+    // no code takes keeps an empty slot: no frames, no CTA starts or moves there).
+    int used[3] = {-1, -1, -1};
+    bool fast = true;
+    for (int c = 0; c < n_codes && fast; ++c) {
+        const int k = kind_of(codes[c]);
+        const int sl = k == kK6R3 ? 0 : (k == kK8R4 ? 1 : (k == kK32R3 ? 2 : -1));
+        if (sl < 0 || used[sl] >= 0) fast = false;
+        else used[sl] = c;
+    }
+    const lpdec_code *slot_codes[3];
+    std::vector<int32_t> slot_frame_code;
+    if (fast) {
+        for (int sl = 0; sl < 3; ++sl) slot_codes[sl] = codes[used[sl] >= 0 ? used[sl] : 0];
+        int slot_of[kMaxMixedCodes];
+        for (int sl = 0; sl < 3; ++sl)
+            if (used[sl] >= 0) slot_of[used[sl]] = sl;
+        slot_frame_code.resize((size_t)n_frames);
+        for (int f = 0; f < n_frames; ++f) slot_frame_code[f] = slot_of[frame_code[f]];
+        codes = slot_codes;
+        n_codes = 3;
+        frame_code = slot_frame_code.data();
+    }
 
     // per-frame offsets and per-code frame lists
     S.n_frames = n_frames;
@@ -277,11 +322,9 @@ int mixed_setup(const char *who, const lpdec_code *const *codes, int32_t n_codes
             }
         }
     }
-    bool fast = true;
-    for (int c = 0; c < n_codes; ++c) {
-        const int k = a.code[c].kind;
-        fast = fast && (k == kK6R3 || k == kK8R4 || k == kK32R3);
-    }
+    if (fast)
+        for (int sl = 0; sl < 3; ++sl)
+            if (used[sl] < 0) a.code[sl].idx_off = -1;  // an empty slot stages nothing
     S.fn = mixed_fn(p->state_dtype, fast);
     cudaError_t err = cudaFuncSetAttribute(S.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return cuda_error(err, "mixed decode: cudaFuncSetAttribute");

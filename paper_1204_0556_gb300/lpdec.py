@@ -28,9 +28,10 @@ LPDEC_ECLOSED = -6
 LPDEC_FRAME_BAD_LLR = -1
 LPDEC_FRAME_ABANDONED = -2
 
-STATE_F32, STATE_BF16, STATE_F16 = 0, 1, 2
+STATE_F32, STATE_BF16, STATE_F16, STATE_Q16 = 0, 1, 2, 3
 SCHED_AUTO, SCHED_STREAMED, SCHED_RESIDENT = 0, 1, 2
-_DTYPES = {"f32": STATE_F32, "fp32": STATE_F32, "bf16": STATE_BF16, "f16": STATE_F16, "fp16": STATE_F16}
+_DTYPES = {"f32": STATE_F32, "fp32": STATE_F32, "bf16": STATE_BF16, "f16": STATE_F16, "fp16": STATE_F16,
+           "q16": STATE_Q16}
 _SCHEDS = {"auto": SCHED_AUTO, "streamed": SCHED_STREAMED, "resident": SCHED_RESIDENT}
 
 # Every symbol include/lpdec.h declares (checked by the CPU test suite).

@@ -205,6 +205,32 @@ def test_fp16_state(gpu, oracle_mod, c1056, snr, seed):
 
 @pytest.mark.parametrize("name,hseed", [("C1056", 0), ("C4000", 2)])
 @pytest.mark.parametrize("snr,seed", [(2.5, 200), (4.0, 201)])
+def test_q16_state(gpu, oracle_mod, name, hseed, snr, seed):
+    """16-bit fixed-point storage of the edge state (FP32 arithmetic) on the
+    precision workload's codes and Eb/N0 points: every frame within 5e-3 of
+    the FP64 oracle after 300 fixed iterations (frames that never converge
+    included), bits and certificates identical on clean frames, word error rate
+    inside the oracle's binomial 95% interval."""
+    code = I.benchmark_code(name, hseed)
+    F = 48
+    llr = I.awgn_llr(code, snr, F, seed)
+    kw = dict(mu=MU, rho=RHO, eps=0.0, max_iter=300)
+    got = gpu_decode(gpu, code, llr, state="q16", **kw)
+    ref = oracle_decode(oracle_mod, code, llr, **kw)
+    err = np.abs(got["x"] - ref["x"]).max(axis=1)
+    print(f"q16 {name} {snr} dB: max|x - x_oracle| {err.max():.3e}, frames above 1e-3: {(err > 1e-3).sum()}/{F}")
+    assert err.max() <= 5e-3
+    clean = clean_frames(ref) & (np.abs(ref["x"] - 0.5).min(axis=1) > 1e-2)
+    assert np.array_equal(got["bits"][clean], ref["bits"][clean])
+    assert np.array_equal(got["cert"][clean], ref["cert"][clean])
+    k_gpu = int(got["bits"].any(axis=1).sum())
+    k_ref = int(ref["bits"].any(axis=1).sum())
+    lo, hi = _wilson(k_ref, F)
+    assert lo <= k_gpu / F <= hi
+
+
+@pytest.mark.parametrize("name,hseed", [("C1056", 0), ("C4000", 2)])
+@pytest.mark.parametrize("snr,seed", [(2.5, 200), (4.0, 201)])
 @pytest.mark.parametrize("state", ["bf16", "f16"])
 def test_16bit_state_error_stated(gpu, oracle_mod, name, hseed, snr, seed, state):
     """BF16 and FP16 storage of the edge state (FP32 arithmetic) against the FP64
@@ -233,7 +259,7 @@ def test_16bit_state_error_stated(gpu, oracle_mod, name, hseed, snr, seed, state
     assert lo <= k_gpu / F <= hi
 
 
-@pytest.mark.parametrize("state", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("state", ["f32", "bf16", "f16", "q16"])
 def test_streamed_equals_resident(gpu, c1056, state):
     llr = I.awgn_llr(c1056, 2.0, 50, 7)
     a = gpu_decode(gpu, c1056, llr, eps=1e-5, max_iter=120, state=state, schedule="resident")
@@ -293,7 +319,7 @@ def test_streamed_tile_equals_resident(gpu, name, state, eps):
 
     code = _shape(name)
     llr = I.awgn_llr(code, 2.5, 40 if name == "C1056" else 12, 606)
-    dt = {"f32": 0, "bf16": 1, "f16": 2}[state]
+    dt = {"f32": 0, "bf16": 1, "f16": 2, "q16": 3}[state]
     d_llr = torch.from_numpy(llr).cuda()
     C = gpu.Code(code)
     try:
@@ -354,6 +380,8 @@ RING_CASES = [
     ("S16V4", "f32", 0.0, 13, [(2, 3)]),
     ("R20", "f32", 1e-5, 17, [(3, 5)]),
     ("C8000", "f16", 1e-5, 7, [(1, 2)]),
+    ("C1056", "q16", 1e-5, 29, [(4, 6)]),
+    ("C4000", "q16", 0.0, 9, [(1, 2)]),
     ("O601", "f32", 1e-5, 23, [(3, 5)]),  # the slots hold no LLR rows (4n not a multiple of 16)
 ]
 
@@ -370,7 +398,7 @@ def test_ring_equals_resident(gpu, name, state, eps, frames, rings):
     code = _shape(name)
     llr = I.awgn_llr(code, 2.5, frames, 707)
     llr[frames // 2, 3] = np.nan
-    dt = {"f32": 0, "bf16": 1, "f16": 2}[state]
+    dt = {"f32": 0, "bf16": 1, "f16": 2, "q16": 3}[state]
     d_llr = torch.from_numpy(llr).cuda()
     C = gpu.Code(code)
     try:
