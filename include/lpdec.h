@@ -377,6 +377,19 @@ LPDEC_API int lpdec_project(int32_t d, int64_t count, const float *v, float *z, 
  */
 LPDEC_API int lpdec_release_memory(void);
 
+/*
+ * Failure handling: the limit, in SM clock cycles, of the first wait of a
+ * STREAMED launch on the bulk copies of a frame's parked state or on a ring
+ * slot.  When such a wait runs out, the frame is marked LPDEC_FRAME_ABANDONED
+ * and the group stops; the copies already in flight are then waited for with
+ * the default limit, so the launch always ends with no copy outstanding.
+ * clocks <= 0 restores the default, 2^31 cycles (about 1 s).  The paper has
+ * no counterpart: the call exists so that the abandonment path can be
+ * exercised (a tiny limit makes the waits run out) without faulting a GPU.
+ * Process-wide; it applies to decodes queued after it.  Never fails.
+ */
+LPDEC_API int lpdec_set_wait_limit(int64_t clocks);
+
 /* ---- dual subgradient decoding (appendix) ------------------------------- */
 
 /*

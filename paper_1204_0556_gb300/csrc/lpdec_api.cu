@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -563,8 +564,13 @@ int validate_params(const lpdec_params *p) {
     return LPDEC_OK;
 }
 
+// Limit of the first wait on a copy or a ring slot in STREAMED launches
+// (lpdec_set_wait_limit); the device-side default is kWaitClocks.
+static std::atomic<long long> g_wait_clocks{kWaitClocks};
+
 IterCfg make_cfg(const lpdec_code *c, const lpdec_params *p) {
     IterCfg cfg;
+    cfg.wait_clocks = g_wait_clocks.load();
     cfg.mu_inv = (float)(1.0 / p->mu);
     cfg.rho = (float)p->rho;
     cfg.rho_inv = (float)(1.0 / p->rho);
@@ -1035,5 +1041,10 @@ extern "C" int lpdec_project(int32_t d, int64_t count, const float *v, float *z,
         default: err = lpdec::launch_project_32(d, count, v, z, s); break;
     }
     if (err != cudaSuccess) return cuda_error(err, "lpdec_project launch");
+    return LPDEC_OK;
+}
+
+extern "C" int lpdec_set_wait_limit(int64_t clocks) {
+    lpdec::g_wait_clocks.store(clocks > 0 ? (long long)clocks : lpdec::kWaitClocks);
     return LPDEC_OK;
 }

@@ -318,6 +318,7 @@ struct IterCfg {
     int max_iter;
     int check_stop;     // eps > 0
     QScale q;           // q16_t state only: the fixed-point scale
+    long long wait_clocks;  // STREAMED: limit of a first wait on a copy or a ring slot (kWaitClocks)
 };
 
 struct DecodeArgs {
@@ -745,10 +746,15 @@ __device__ __forceinline__ float llr_at(const float *g, const float *gs, int i) 
 
 // Wait for the mbarrier phase with the given parity, for at most ~1 s of SM
 // clocks; returns false on timeout (the caller reports it, never spins forever).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+// The first wait on a copy or a slot takes the decode's limit
+// (IterCfg::wait_clocks, normally kWaitClocks); the wait for copies still in
+// flight after a timeout always takes kWaitClocks, so no CTA leaves while a
+// copy into its shared memory may still land.
+constexpr long long kWaitClocks = 1ll << 31;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long limit = kWaitClocks) {
     const long long start = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - start > (1ll << 31)) return false;
+        if (clock64() - start > limit) return false;
     }
     return true;
 }
@@ -841,7 +847,7 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
             mbar_arrive_expect_tx(sm.mbar, 2u * (uint32_t)state_bytes);
             bulk_load(sm.w, zg, (uint32_t)state_bytes, sm.mbar);
             bulk_load(sm.l, lg, (uint32_t)state_bytes, sm.mbar);
-            flags[3] = mbar_wait_bounded(sm.mbar, phase) ? 1 : 0;
+            flags[3] = mbar_wait_bounded(sm.mbar, phase, p.wait_clocks) ? 1 : 0;
         }
         group_sync(bar, T);
         if (flags[3] == 0) {
@@ -1130,10 +1136,10 @@ struct RingMeta {
 };
 
 // Wait (bounded like mbar_wait_bounded) until a slot's tag holds `seq`.
-__device__ __forceinline__ bool ring_wait_tag(const int *tag, int seq) {
+__device__ __forceinline__ bool ring_wait_tag(const int *tag, int seq, long long limit) {
     const long long start = clock64();
     while (*reinterpret_cast<const volatile int *>(tag) != seq) {
-        if (clock64() - start > (1ll << 31)) return false;
+        if (clock64() - start > limit) return false;
     }
     return true;
 }
@@ -1148,18 +1154,27 @@ constexpr int kRingClaim = 4;  // frames the producer claims per atomic while ma
 // Publish frame f (k iterations done; f < 0: no more frames) as sequence
 // number seq of the ring: wait until its slot is free, then start the bulk
 // copies of the parked state (k > 0) and of the frame's LLRs (when the slots
-// hold them), or mark the slot ready at once.  Run by one thread; false if the
-// wait for the slot ran out or a group stopped.
+// hold them), or mark the slot ready at once.  Run by one thread.  Returns
+// kPubNone if nothing was published (the wait for the slot ran out or a group
+// had stopped), kPubOk, or kPubStop: published, but a group has stopped.
+//
+// A group that gives up on its slot's tag sets the stop flag and then reads
+// the tag; the producer writes the tag and then reads the stop flag.  With a
+// block-scope SC fence between the write and the read on both sides, at least
+// one of them sees the other's write: the group (tag seen) waits for the
+// copies itself, or the producer (stop seen) counts the publish among those
+// whose copies it waits for before leaving.
+constexpr int kPubNone = 0, kPubOk = 1, kPubStop = 2;
 template <typename S>
-__device__ __forceinline__ bool ring_publish(const DecodeArgs &a, unsigned char *smem_raw, RingMeta *meta,
-                                             volatile int *abort_flag, int seq, int f, int k) {
+__device__ __forceinline__ int ring_publish(const DecodeArgs &a, unsigned char *smem_raw, RingMeta *meta,
+                                            volatile int *abort_flag, int seq, int f, int k) {
     const int R = a.ring_slots;
     const int s = seq % R;
-    if (seq >= R && !mbar_wait_bounded(&meta[s].empty, (uint32_t)(seq / R - 1) & 1u)) {
+    if (seq >= R && !mbar_wait_bounded(&meta[s].empty, (uint32_t)(seq / R - 1) & 1u, a.cfg.wait_clocks)) {
         *abort_flag = 1;
-        return false;
+        return kPubNone;
     }
-    if (*abort_flag) return false;
+    if (*abort_flag) return kPubNone;
     meta[s].frame = f;
     *reinterpret_cast<volatile int *>(&meta[s].seq) = seq;  // the tag groups wait for (ring_wait_tag)
     const uint32_t sbytes = (uint32_t)((size_t)a.code.Ep * sizeof(S));
@@ -1180,7 +1195,8 @@ __device__ __forceinline__ bool ring_publish(const DecodeArgs &a, unsigned char 
     } else {
         mbar_arrive(&meta[s].full);
     }
-    return true;
+    __threadfence_block();
+    return *abort_flag ? kPubStop : kPubOk;
 }
 
 // The producer warp: claims frames in batches (one atomic per batch, the
@@ -1211,16 +1227,19 @@ __device__ void ring_produce(const DecodeArgs &a, unsigned char *smem_raw, RingM
             live &= live - 1;
             const int fs = __shfl_sync(full, f, src);
             const int ks = __shfl_sync(full, k, src);
-            if (lane == 0) ok = ring_publish<S>(a, smem_raw, meta, abort_flag, seq, fs, ks) ? 1 : 0;
-            ok = __shfl_sync(full, ok, 0);
-            seq += ok;
+            int st = kPubNone;
+            if (lane == 0) st = ring_publish<S>(a, smem_raw, meta, abort_flag, seq, fs, ks);
+            st = __shfl_sync(full, st, 0);
+            seq += st != kPubNone;
+            ok = st == kPubOk;
         }
         if (!ok) break;
     }
     if (lane != 0) return;
     for (int i = 0; i < G && ok; ++i) {  // one "no more frames" slot per group
-        ok = ring_publish<S>(a, smem_raw, meta, abort_flag, seq, -1, 0) ? 1 : 0;
-        seq += ok;
+        const int st = ring_publish<S>(a, smem_raw, meta, abort_flag, seq, -1, 0);
+        seq += st != kPubNone;
+        ok = st == kPubOk;
     }
     // After a stop, the copies of the last R published slots may be in flight:
     // wait for them (bounded) before the CTA can exit.
@@ -1287,7 +1306,8 @@ __global__ void __launch_bounds__(MAXT, 1) decode_kernel_ring(const DecodeArgs a
         // group releases it); a mismatch is a broken invariant and stops the
         // group like a timeout.
         if (t == 0)
-            sm.flags[3] = (ring_wait_tag(&meta[s].seq, my) && mbar_wait_bounded(&meta[s].full, ph) &&
+            sm.flags[3] = (ring_wait_tag(&meta[s].seq, my, a.cfg.wait_clocks) &&
+                           mbar_wait_bounded(&meta[s].full, ph, a.cfg.wait_clocks) &&
                            *reinterpret_cast<const volatile int *>(&meta[s].seq) == my)
                               ? 1
                               : 0;
@@ -1295,7 +1315,9 @@ __global__ void __launch_bounds__(MAXT, 1) decode_kernel_ring(const DecodeArgs a
         if (sm.flags[3] == 0) {
             if (t == 0) {
                 *abort_flag = 1;
-                if (meta[s].seq == my && meta[s].frame >= 0) {  // published, copies late
+                __threadfence_block();  // pairs with the producer's fence in ring_publish
+                if (*reinterpret_cast<const volatile int *>(&meta[s].seq) == my && meta[s].frame >= 0) {
+                    // published, copies late
                     mbar_wait_bounded(&meta[s].full, ph);
                     const int f = meta[s].frame;
                     if (a.iters_out) a.iters_out[f] = kFrameTimeout;

@@ -73,7 +73,10 @@ __device__ __forceinline__ void mixed_round(const MixedCode &mc, const CodeView 
         io.cert = b.cert_out ? b.cert_out + f : nullptr;
         io.w_state = io.l_state = nullptr;
         io.k_state = nullptr;
-        frame_run<D, L, DV, S>(cv, mc.cfg, mc.cfg.max_iter, io, sm, t, T, bar, phase);
+        // (3,6) codes stage their 16-bit indices in the mixed CTA; the others,
+        // whose frames fill the shared memory, read them from global memory
+        // with the x-update's prefetch (as the single-code kernels do)
+        frame_run<D, L, DV, S, false, !(DV == 3 && D <= 8)>(cv, mc.cfg, mc.cfg.max_iter, io, sm, t, T, bar, phase);
     }
 }
 

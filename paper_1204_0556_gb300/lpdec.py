@@ -44,7 +44,7 @@ EXPORTED = [
     "lpdec_server_stats", "lpdec_server_destroy", "lpdec_autotune", "lpdec_set_tile", "lpdec_server_counters",
     "lpdec_mixed_plan_create", "lpdec_mixed_plan_decode", "lpdec_mixed_plan_destroy",
     "lpdec_decode_dual", "lpdec_dual_set_tile", "lpdec_set_streamed_tile", "lpdec_get_tile",
-    "lpdec_release_memory",
+    "lpdec_release_memory", "lpdec_set_wait_limit",
 ]
 
 
@@ -122,6 +122,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
             "lpdec_set_streamed_tile": (ctypes.c_int, [_vp, _i32, _i32, _i32, _i32]),
             "lpdec_get_tile": (ctypes.c_int, [_vp, _i32, _i32, _i32p, _i32p, _i32p]),
             "lpdec_release_memory": (ctypes.c_int, []),
+            "lpdec_set_wait_limit": (ctypes.c_int, [_i64]),
         })
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -268,6 +269,12 @@ def lpdec_set_streamed_tile(handle: int, state_dtype: int, group_threads: int, g
 
 def lpdec_release_memory() -> None:
     _check(load().lpdec_release_memory())
+
+
+def lpdec_set_wait_limit(clocks: int) -> None:
+    """Limit (SM clocks) of a STREAMED launch's first wait on a copy or a ring
+    slot; clocks <= 0 restores the default (2^31)."""
+    _check(load().lpdec_set_wait_limit(int(clocks)))
 
 
 def lpdec_get_tile(handle: int, state_dtype: int, schedule: int) -> dict:
