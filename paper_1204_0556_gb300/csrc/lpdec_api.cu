@@ -235,8 +235,14 @@ extern "C" int lpdec_code_create(int32_t n, int32_t m, const int32_t *row_ptr, c
         std::vector<uint16_t> h16((size_t)c->idx16_bytes / 2, 0);
         for (int64_t e = 0; e < E; ++e) h16[(size_t)e] = (uint16_t)col_idx[e];
         uint16_t *csc = h16.data() + c->col16_elems;
+        // (4,8) form: the edge state sits at the swizzled position of each
+        // edge (lpdec::state_pos), so the variable phase gathers from there.
+        const bool swz = lpdec::kClassD[c->cls] == 8;
         for (int i = 0; i < n; ++i)
-            for (int s = col_ptr[i]; s < col_ptr[i + 1]; ++s) csc[(size_t)i * 4 + (s - col_ptr[i])] = (uint16_t)edge_perm[s];
+            for (int s = col_ptr[i]; s < col_ptr[i + 1]; ++s) {
+                const int e = edge_perm[s];
+                csc[(size_t)i * 4 + (s - col_ptr[i])] = (uint16_t)(swz ? lpdec::state_pos8(e) : e);
+            }
         order_edge_slots(csc, n, c->reg_dv);
         err = cudaMalloc(&c->dev_idx16, (size_t)c->idx16_bytes);
         if (err == cudaSuccess)

@@ -383,6 +383,18 @@ __device__ __forceinline__ float warp_max(float v) {
 template <typename S>
 constexpr bool kFoldX = std::is_same<S, float>::value;
 
+// Position of an edge's state in the (4,8) regular form.  With one thread per
+// check, a warp's checks j0..j0+31 start 8 words apart, so the paired 8-byte
+// accesses of the check update would meet the same banks every fourth check
+// (a 4-way conflict).  The pair slot of edge k of check j is therefore XORed
+// with (j >> 2) & 3: within each half warp, the four checks that share a bank
+// group use four different pair slots, and every paired load and store of the
+// check update takes the minimum of two wavefronts.  The variable phase
+// gathers through the 16-bit edge ids, which hold these positions.
+__host__ __device__ constexpr int state_pos8(int e) {
+    return (e & ~7) | ((((e >> 1) & 3) ^ ((e >> 5) & 3)) << 1) | (e & 1);
+}
+
 // RES: also accumulate the primal and dual residual terms (iterations that run
 // the stopping test or produce the certificate); without them z_old is not
 // needed and v = rho x + (1 - rho) w + (2 - rho) lambda/mu directly.
@@ -396,12 +408,16 @@ __device__ __forceinline__ void check_update(const CodeView &c, const IterCfg &p
     const int d = kReg ? D : __ldg(c.row_ptr + j + 1) - e0;
     float v[D];
     float xv[kKeep ? D : 1], zo[kKeep ? D : 1];
+    // (4,8) form: pair slot k/2 of check j sits at slot (k/2) ^ ((j >> 2) & 3) (state_pos8)
+    constexpr bool kSwz = kPairs && D == 8;
+    const int sw = kSwz ? ((j >> 2) & 3) : 0;
     if constexpr (kPairs) {
         const uint32_t *ci = reinterpret_cast<const uint32_t *>(c.col16 + e0);
 #pragma unroll
         for (int k = 0; k < D; k += 2) {
-            const float2 w2 = ld2<S>(ws + e0 + k, p.q);  // u = rho x + (1 - rho) w when folded
-            const float2 l2 = ld2<S>(ls + e0 + k, p.q);
+            const int ks = kSwz ? 2 * ((k >> 1) ^ sw) : k;
+            const float2 w2 = ld2<S>(ws + e0 + ks, p.q);  // u = rho x + (1 - rho) w when folded
+            const float2 l2 = ld2<S>(ls + e0 + ks, p.q);
             if constexpr (!RES && kFoldX<S>) {  // regular form (kPairs): ws holds u
                 const float2 vv = __ffma2_rn(make_float2(p.tmr, p.tmr), l2, w2);  // packed pair, lane = fmaf
                 v[k] = vv.x;
@@ -451,8 +467,9 @@ __device__ __forceinline__ void check_update(const CodeView &c, const IterCfg &p
             const float2 zz = make_float2(z0, z1);
             const float2 ll = __ffma2_rn(zz, m1, make_float2(v[k], v[k + 1]));
             const float2 ww = __ffma2_rn(ll, m1, zz);
-            st2<S>(ls + e0 + k, ll.x, ll.y, p.q);
-            st2<S>(ws + e0 + k, ww.x, ww.y, p.q);
+            const int ks = kSwz ? 2 * ((k >> 1) ^ sw) : k;
+            st2<S>(ls + e0 + ks, ll.x, ll.y, p.q);
+            st2<S>(ws + e0 + ks, ww.x, ww.y, p.q);
             if constexpr (RES) {
                 float a = xv[k] - z0, b = z0 - zo[k];
                 rp = fmaf(a, a, rp);

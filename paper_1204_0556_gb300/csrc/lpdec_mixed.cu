@@ -86,12 +86,14 @@ __device__ __noinline__ void mixed_round_call(const MixedCode *mc, MixedIO b, un
     mixed_round<D, L, DV, S>(*mc, mc->view, b, smem_raw, g, t);
 }
 
-// FAST kernel: mc is a descriptor of the kernel's parameter block; only the
-// staged index pointers are rebuilt here.
-template <int D, int L, int DV, typename S>
+// FAST kernel: mc is a descriptor of the kernel's parameter block.  STAGED:
+// the code's 16-bit indices were copied to shared memory at mc.idx_off (the
+// pointers are rebuilt here); otherwise they stay the global ones, so each
+// instantiation knows the memory its index loads go to.
+template <int D, int L, int DV, typename S, bool STAGED>
 __device__ __forceinline__ void fast_round(const MixedCode &mc, MixedIO b, unsigned char *smem_raw, int g, int t) {
     CodeView cv = mc.view;
-    if (mc.idx_off >= 0) {
+    if constexpr (STAGED) {
         cv.col16 = reinterpret_cast<const uint16_t *>(smem_raw + mc.idx_off);
         cv.csc16 = cv.col16 + mc.view.col16_elems;
     }
@@ -126,10 +128,13 @@ __global__ void __launch_bounds__(kMixedMaxThreads, 1) mixed_kernel(const MixedA
             MixedIO b{a.offset, a.llr, a.x_out, a.bits_out, a.iters_out, a.cert_out, a.queues + cur};
             const int t = threadIdx.x - g * T;
             if constexpr (FAST) {
-                switch (cur) {  // slot s holds the code of FAST form s
-                    case 0: fast_round<6, 1, 3, S>(a.code[0], b, smem_raw, g, t); break;
-                    case 1: fast_round<8, 1, 4, S>(a.code[1], b, smem_raw, g, t); break;
-                    default: fast_round<32, class_lanes(32), 3, S>(a.code[2], b, smem_raw, g, t); break;
+                switch (cur) {  // slot s holds the code of FAST form s; slots 1 and 2 never stage
+                    case 0:
+                        if (a.code[0].idx_off >= 0) fast_round<6, 1, 3, S, true>(a.code[0], b, smem_raw, g, t);
+                        else fast_round<6, 1, 3, S, false>(a.code[0], b, smem_raw, g, t);
+                        break;
+                    case 1: fast_round<8, 1, 4, S, false>(a.code[1], b, smem_raw, g, t); break;
+                    default: fast_round<32, class_lanes(32), 3, S, false>(a.code[2], b, smem_raw, g, t); break;
                 }
             } else {
                 switch (cur_code.kind) {
@@ -325,9 +330,12 @@ int mixed_setup(const char *who, const lpdec_code *const *codes, int32_t n_codes
             }
         }
     }
+    // FAST: an empty slot stages nothing, and the (4,8) and wide slots never
+    // stage (their frames fill the shared memory; their kernel forms read the
+    // indices from global memory with the x-update's prefetch)
     if (fast)
         for (int sl = 0; sl < 3; ++sl)
-            if (used[sl] < 0) a.code[sl].idx_off = -1;  // an empty slot stages nothing
+            if (used[sl] < 0 || sl > 0) a.code[sl].idx_off = -1;
     S.fn = mixed_fn(p->state_dtype, fast);
     cudaError_t err = cudaFuncSetAttribute(S.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return cuda_error(err, "mixed decode: cudaFuncSetAttribute");
