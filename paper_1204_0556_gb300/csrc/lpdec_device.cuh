@@ -1445,7 +1445,7 @@ struct MixedCode {
 struct MixedArgs {
     int n_codes;
     MixedCode code[kMaxMixedCodes];
-    int home_end[kMaxMixedCodes];  // CTA b starts on the first code c with b < home_end[c]
+    int order[kMaxMixedCodes];     // codes by decreasing edges per frame: CTAs take them in this order
     const long long *offset;       // [F] element offset of frame f in llr, x_out and bits_out
     const float *llr;
     float *x_out;

@@ -105,8 +105,13 @@ __global__ void __launch_bounds__(kMixedMaxThreads, 1) mixed_kernel(const MixedA
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int next_code;
     __shared__ MixedCode cur_code;  // descriptor of the code this CTA works on
-    int cur = 0;
-    while (cur < a.n_codes - 1 && (int)blockIdx.x >= a.home_end[cur]) ++cur;
+    // Longest frames first: every CTA starts on the code with the most edges
+    // per frame and moves through the codes in that order, so the frames still
+    // running when the batch drains are those of the shortest code.
+    int cur = -1;
+    for (int q = 0; q < a.n_codes && cur < 0; ++q)
+        if (a.code[a.order[q]].n_frames > 0) cur = a.order[q];
+    if (cur < 0) return;
     for (;;) {
         if (threadIdx.x == 0) cur_code = a.code[cur];
         __syncthreads();
@@ -153,10 +158,10 @@ __global__ void __launch_bounds__(kMixedMaxThreads, 1) mixed_kernel(const MixedA
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            // next code with frames left, starting after the current one
+            // the first code, in the order above, that still has frames
             int nx = -1;
-            for (int q = 1; q <= a.n_codes; ++q) {
-                const int c = (cur + q) % a.n_codes;
+            for (int q = 0; q < a.n_codes; ++q) {
+                const int c = a.order[q];
                 if (atomicAdd(a.queues + c, 0) < a.code[c].n_frames) { nx = c; break; }
             }
             next_code = nx;
@@ -346,15 +351,9 @@ int mixed_setup(const char *who, const lpdec_code *const *codes, int32_t n_codes
     S.grid = bps * device_sm_count(dev);
     S.block = block;
     S.smem = smem;
-    // home codes: CTAs split in proportion to each code's edge work
-    double total = 0.0;
-    for (int c = 0; c < n_codes; ++c) total += (double)a.code[c].n_frames * codes[c]->E;
-    double run = 0.0;
-    for (int c = 0; c < n_codes; ++c) {
-        run += (double)a.code[c].n_frames * codes[c]->E;
-        const int acc = (int)std::lround(S.grid * (total > 0 ? run / total : 1.0));
-        a.home_end[c] = c == n_codes - 1 ? S.grid : acc;
-    }
+    // the order in which CTAs take the codes: most edges per frame first
+    for (int c = 0; c < n_codes; ++c) a.order[c] = c;
+    std::stable_sort(a.order, a.order + n_codes, [&](int x, int y) { return codes[x]->E > codes[y]->E; });
     return LPDEC_OK;
 }
 
