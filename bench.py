@@ -172,7 +172,12 @@ def hand_ops_per_frame_iter(code) -> int:
 # traffic: dram__bytes_read.sum + dram__bytes_write.sum of one launch of
 # traffic_frames frames (the bench's full-size launch where it was captured).
 KERNEL_SOURCES = ("lpdec_device.cuh", "lpdec_kclass.cuh", "lpdec_internal.h")
-MEASURED_COUNTERS = {}
+MEASURED_COUNTERS = {
+    # C1056, 8000 frames x 300 iterations, tile 6 x 160 (instruction counters); traffic from the
+    # bench's full-size launch (4 x 10^4 frames, tile 6 x 160)
+    "C1056/resident/f32": {"hash": "5295e5d49ff08db1", "fp32_ops": 53835, "warp_inst": 3957.4,
+                           "traffic": 175_607_040 + 165_057_024, "traffic_frames": 40000},
+}
 
 
 def kernel_source_hash() -> str:
