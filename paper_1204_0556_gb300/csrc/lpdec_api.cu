@@ -124,6 +124,50 @@ static void order_edge_slots(uint16_t *csc, int n, int dv) {
     }
 }
 
+// Processing order of the checks of a wide code whose check degrees differ.
+// A warp's 16 lane pairs take 16 consecutive entries of the order, and pair p
+// reads words e0_p + 2k and e0_p + 2k + 1 of the edge state (e0_p: its check's
+// first edge), so the warp's accesses fall in distinct banks when the 16
+// offsets share a parity and are distinct mod 32.  The checks are bucketed by
+// e0 mod 32 and dealt out in groups of 16, one per bucket of a parity, fullest
+// buckets first; groups are padded from the fullest buckets when a parity runs
+// short.  (C8000: 2.7 -> 1.2 wavefronts per check-update access, simulated;
+// 2.67e11 -> 2.74e11 edge-iterations/s measured at 300 iterations.)
+// Only the order in which checks are taken changes, not what is computed.
+static void check_order_for_banks(int m, const int32_t *row_ptr, int32_t *order) {
+    std::vector<std::vector<int32_t>> bucket(32);
+    for (int j = m - 1; j >= 0; --j) bucket[row_ptr[j] & 31].push_back(j);  // popped in index order
+    int pos = 0;
+    for (int par = 0; par < 2; ++par) {
+        auto left = [&] {
+            for (int r = par; r < 32; r += 2)
+                if (!bucket[r].empty()) return true;
+            return false;
+        };
+        while (left()) {
+            int rs[16], nr = 0;
+            for (int r = par; r < 32; r += 2) rs[nr++] = r;
+            std::stable_sort(rs, rs + nr, [&](int a, int b) { return bucket[a].size() > bucket[b].size(); });
+            int taken = 0;
+            for (int q = 0; q < nr && taken < 16; ++q)
+                if (!bucket[rs[q]].empty()) {
+                    order[pos++] = bucket[rs[q]].back();
+                    bucket[rs[q]].pop_back();
+                    ++taken;
+                }
+            while (taken < 16) {  // this parity runs short: fill from its fullest buckets
+                int best = -1;
+                for (int r = par; r < 32; r += 2)
+                    if (!bucket[r].empty() && (best < 0 || bucket[r].size() > bucket[best].size())) best = r;
+                if (best < 0) break;
+                order[pos++] = bucket[best].back();
+                bucket[best].pop_back();
+                ++taken;
+            }
+        }
+    }
+}
+
 extern "C" int lpdec_code_create(int32_t n, int32_t m, const int32_t *row_ptr, const int32_t *col_idx,
                                  const int32_t *col_ptr, const int32_t *row_idx, const int32_t *edge_perm,
                                  lpdec_code **out) {
@@ -204,10 +248,13 @@ extern "C" int lpdec_code_create(int32_t n, int32_t m, const int32_t *row_ptr, c
     }
     cudaError_t err = cudaGetDevice(&c->device);
     if (err != cudaSuccess) { delete c; return cuda_error(err, "lpdec_code_create: cudaGetDevice"); }
-    // Four index arrays in one allocation, each starting on a 16-byte boundary.
+    // Four index arrays in one allocation, each starting on a 16-byte boundary,
+    // plus (wide classes with differing check degrees) the check order.
     auto pad4 = [](size_t w) { return (w + 3) & ~(size_t)3; };
+    const bool ordered = lpdec::kClassD[c->cls] > 8 && c->reg_dc == 0;
     const size_t o_row = 0, o_col = pad4((size_t)m + 1), o_cptr = o_col + pad4((size_t)E),
-                 o_csc = o_cptr + pad4((size_t)n + 1), words = o_csc + pad4((size_t)E);
+                 o_csc = o_cptr + pad4((size_t)n + 1), o_ord = o_csc + pad4((size_t)E),
+                 words = o_ord + (ordered ? pad4((size_t)m) : 0);
     err = cudaMalloc(&c->dev_block, words * sizeof(int32_t));
     if (err != cudaSuccess) { delete c; return cuda_error(err, "lpdec_code_create: cudaMalloc"); }
     int32_t *p = static_cast<int32_t *>(c->dev_block);
@@ -215,7 +262,9 @@ extern "C" int lpdec_code_create(int32_t n, int32_t m, const int32_t *row_ptr, c
     c->col_idx = p + o_col;
     c->col_ptr = p + o_cptr;
     c->csc_edge = p + o_csc;
+    c->check_order = ordered ? p + o_ord : nullptr;
     std::vector<int32_t> host(words, 0);
+    if (ordered) check_order_for_banks(m, row_ptr, host.data() + o_ord);
     std::copy(row_ptr, row_ptr + m + 1, host.begin() + o_row);
     std::copy(col_idx, col_idx + E, host.begin() + o_col);
     std::copy(col_ptr, col_ptr + n + 1, host.begin() + o_cptr);
@@ -606,6 +655,7 @@ CodeView make_view(const lpdec_code *c) {
     v.E = c->E;
     v.Ep = c->Ep;
     v.row_ptr = c->row_ptr;
+    v.check_order = c->check_order;
     v.col_idx = c->col_idx;
     v.col_ptr = c->col_ptr;
     v.csc_edge = c->csc_edge;

@@ -64,6 +64,7 @@ struct lpdec_code {
     int reg_dc = 0;             // its common check degree, or 0 when check degrees differ (wide classes)
     void *dev_block = nullptr;  // one allocation holding the four index arrays
     int32_t *row_ptr = nullptr, *col_idx = nullptr, *col_ptr = nullptr, *csc_edge = nullptr;
+    int32_t *check_order = nullptr;  // wide classes with differing check degrees (see CodeView), else null
     // Regular codes: 16-bit index block (CodeView::col16 / csc16), else null.
     void *dev_idx16 = nullptr;
     int idx16_bytes = 0, col16_elems = 0;

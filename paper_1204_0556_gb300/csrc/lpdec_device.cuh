@@ -304,6 +304,8 @@ struct CodeView {
     int col16_elems;
     int reg_dc;               // regular-code kernels: the common check degree (check j owns edges
                               // j*reg_dc ...), or 0 when check degrees differ (wide classes only)
+    const int *check_order;   // wide classes with differing check degrees: the order in which the
+                              // check phase takes the checks (a permutation of 0..m-1), else null
 };
 
 struct IterCfg {
@@ -956,16 +958,20 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
         float rp = 0.0f, rd = 0.0f;
         if constexpr (D > 8) {
             // L lanes per check; every lane of the group runs the same number of passes
+            // (with check_order, a warp's 16 lane pairs take 16 consecutive entries
+            // of it: see check_order_for_banks)
             const int per_pass = T / L;
             if (need_res) {
                 for (int j0 = 0; j0 < c.m; j0 += per_pass) {
-                    const int j = j0 + t / L;
-                    check_update_w<D, L, DV, S, true>(c, p, j, j < c.m, sm.w, sm.l, sm.x, rp, rd);
+                    const int jj = j0 + t / L;
+                    const int j = (jj < c.m && c.check_order) ? __ldg(c.check_order + jj) : jj;
+                    check_update_w<D, L, DV, S, true>(c, p, j, jj < c.m, sm.w, sm.l, sm.x, rp, rd);
                 }
             } else {
                 for (int j0 = 0; j0 < c.m; j0 += per_pass) {
-                    const int j = j0 + t / L;
-                    check_update_w<D, L, DV, S, false>(c, p, j, j < c.m, sm.w, sm.l, sm.x, rp, rd);
+                    const int jj = j0 + t / L;
+                    const int j = (jj < c.m && c.check_order) ? __ldg(c.check_order + jj) : jj;
+                    check_update_w<D, L, DV, S, false>(c, p, j, jj < c.m, sm.w, sm.l, sm.x, rp, rd);
                 }
             }
         } else {
