@@ -166,8 +166,10 @@ LPDEC_API int lpdec_autotune(lpdec_code *code, const lpdec_params *params, int32
                              void *cuda_stream, int32_t *group_threads, int32_t *groups, double *ms_per_frame);
 
 /* Set a code's tile for one state dtype by hand (groups x group_threads), for
- * both schedules; 0, 0 restores the built-in default.  LPDEC_EINVAL for a tile
- * that does not fit. */
+ * both schedules; 0, 0 restores the built-in default.  group_threads is a
+ * multiple of 32, groups <= 15, and a CTA holds at most 1024 threads (896 for
+ * codes whose checks have degree 17..32, whose kernels are compiled for 896
+ * threads to get more registers).  LPDEC_EINVAL for a tile that does not fit. */
 LPDEC_API int lpdec_set_tile(lpdec_code *code, int32_t state_dtype, int32_t group_threads, int32_t groups);
 
 /* Set a code's STREAMED tile for one state dtype by hand (the RESIDENT tile is

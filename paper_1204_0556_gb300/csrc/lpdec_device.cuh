@@ -519,7 +519,10 @@ __device__ __forceinline__ void check_update(const CodeView &c, const IterCfg &p
 // sum_q max(0, beta - kappa_q) - 1 is convex and increasing, so Newton's step
 // beta <- (1 + sum_{kappa < beta} kappa) / #{kappa < beta} from any point above
 // the root decreases monotonically to it (the tangent lies below h) and stops
-// when the active set stops changing.  It starts from the smaller of two
+// when the active set stops changing.  The pass that takes a step also finds
+// the largest active breakpoint; when the new point lies above it, the active
+// set cannot change and the step is final without another pass (the pass it
+// saves would return the same value).  It starts from the smaller of two
 // points above the root: (1 + sum_q kappa_q) / d, exact when every breakpoint
 // is active, and 1 + kappa_(1), exact when only the smallest one is.
 // DV > 0: the regular form (16-bit column indices; with FP32 state and no
@@ -606,19 +609,23 @@ __device__ __forceinline__ float project_wide(float (&kap)[D / L], int d, int dr
         const unsigned pm = ((1u << L) - 1u) << (threadIdx.x & (32 - L));  // the check's lanes
         beta = fminf(__fdividef(1.0f + ksum, (float)d), 1.0f + k1);
         for (int it = 0; it <= D; ++it) {
-            float s1 = 0.0f;
+            float s1 = 0.0f, kmax = -kBigKappa;
             int cnt = 0;
 #pragma unroll
             for (int k = 0; k < V; ++k)
-                if (kap[k] < beta) { s1 += kap[k]; ++cnt; }
+                if (kap[k] < beta) { s1 += kap[k]; ++cnt; kmax = fmaxf(kmax, kap[k]); }
 #pragma unroll
             for (int o = 1; o < L; o <<= 1) {
                 s1 += __shfl_xor_sync(pm, s1, o);
                 cnt += __shfl_xor_sync(pm, cnt, o);
+                kmax = fmaxf(kmax, __shfl_xor_sync(pm, kmax, o));
             }
             const float nb = __fdividef(1.0f + s1, (float)cnt);  // cnt >= 1: beta > kappa_(1)
             if (!(nb < beta)) break;
             beta = nb;
+            // no breakpoint in [nb, old beta): the active set at nb is the same,
+            // so a further step would return nb again (the same sum, bit for bit)
+            if (nb > kmax) break;
         }
         beta = fmaxf(beta, 0.0f);
     }

@@ -162,7 +162,7 @@ def test_c1056_full_bench_size(gpu, oracle_mod, c1056):
         C.close()
 
 
-@pytest.mark.parametrize("name,seed,tile", [("C4000", 2, (800, 1)), ("C8000", 3, (928, 1))])
+@pytest.mark.parametrize("name,seed,tile", [("C4000", 2, (800, 1)), ("C8000", 3, (800, 1))])
 def test_wide_codes_full_bench_size(gpu, oracle_mod, name, seed, tile):
     """`bench.py --code C4000 | C8000` at full size (4 x 10^4 frames over the four
     Eb/N0 points, 300 fixed iterations, RESIDENT, the bench's tile): sampled
