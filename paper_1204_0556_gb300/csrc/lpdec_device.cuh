@@ -1425,11 +1425,14 @@ namespace lpdec {
 // ---------------------------------------------------------------------------
 // Mixed-code batches: one persistent launch decodes frames of several codes.
 constexpr int kMaxMixedCodes = 8;
-// CTA size bound of the mixed kernel.  Each kernel form runs in its own
-// non-inlined function, so a 1024-thread CTA (64 registers) measured faster
-// than 768 threads with 80 registers.
+// CTA size bound of the mixed kernel: 896 threads, 72 registers a thread.
+// The FAST kernel's inlined wide form spills 44-60 bytes there instead of
+// 120-128 at 1024 threads (64 registers), and a C1056/C2640/C4000 batch runs
+// in 313 ms instead of 354 ms.  (768 threads with 80 registers measured
+// slower than 1024 threads in the general kernel.)  Codes whose tile is wider
+// run fewer frames per CTA in a mixed launch.
 #ifndef LPDEC_MIXED_MAX_THREADS
-#define LPDEC_MIXED_MAX_THREADS 1024
+#define LPDEC_MIXED_MAX_THREADS 896
 #endif
 constexpr int kMixedMaxThreads = LPDEC_MIXED_MAX_THREADS;
 
