@@ -53,7 +53,7 @@ def _load():
         lib.oracle_decode.argtypes = [
             ctypes.c_int, ctypes.c_int, i32p, i32p, ctypes.c_int, ctypes.c_int, dp,
             ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
-            dp, u8p, i32p, u8p, u8p]
+            dp, u8p, i32p, u8p, u8p, dp]
         lib.oracle_lp_max.argtypes = [ctypes.c_int, dp, dp]
         lib.oracle_decode_dual.argtypes = [
             ctypes.c_int, ctypes.c_int, i32p, i32p, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, ctypes.c_int,
@@ -144,7 +144,8 @@ def decode(row_ptr, col_idx, n: int, gamma, mu: float = 3.0, rho: float = 1.9,
     """Algorithm 1 on every frame of ``gamma`` ([frames x n]).
 
     Returns a dict with x (float64), bits (uint8), iters (int32),
-    converged (uint8) and cert (uint8).
+    converged (uint8), cert (uint8), and rp, rd (float64): the primal and dual
+    residuals of Section 3.3 after each frame's last iteration.
     """
     lib = _load()
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
@@ -159,6 +160,7 @@ def decode(row_ptr, col_idx, n: int, gamma, mu: float = 3.0, rho: float = 1.9,
     iters = np.zeros(F, dtype=np.int32)
     conv = np.zeros(F, dtype=np.uint8)
     cert = np.zeros(F, dtype=np.uint8)
+    resid = np.zeros((F, 2), dtype=np.float64)
     threads = max(1, min(threads or default_threads(), F))
 
     def run(lo: int, hi: int) -> int:
@@ -166,7 +168,7 @@ def decode(row_ptr, col_idx, n: int, gamma, mu: float = 3.0, rho: float = 1.9,
             n, m, _ptr(row_ptr, ctypes.c_int32), _ptr(col_idx, ctypes.c_int32), lo, hi,
             _ptr(gamma, ctypes.c_double), mu, rho, eps, max_iter, cert_tol,
             _ptr(x, ctypes.c_double), _ptr(bits, ctypes.c_uint8), _ptr(iters, ctypes.c_int32),
-            _ptr(conv, ctypes.c_uint8), _ptr(cert, ctypes.c_uint8))
+            _ptr(conv, ctypes.c_uint8), _ptr(cert, ctypes.c_uint8), _ptr(resid, ctypes.c_double))
 
     if threads == 1:
         rc = [run(0, F)]
@@ -176,4 +178,5 @@ def decode(row_ptr, col_idx, n: int, gamma, mu: float = 3.0, rho: float = 1.9,
             rc = list(ex.map(lambda t: run(int(edges[t]), int(edges[t + 1])), range(threads)))
     if any(rc):
         raise ValueError("oracle_decode rejected its arguments")
-    return {"x": x, "bits": bits, "iters": iters, "converged": conv, "cert": cert}
+    return {"x": x, "bits": bits, "iters": iters, "converged": conv, "cert": cert,
+            "rp": resid[:, 0].copy(), "rd": resid[:, 1].copy()}

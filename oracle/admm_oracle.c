@@ -199,13 +199,16 @@ int oracle_project_many(int d, int64_t count, const double *v, double *z, int us
  * H is given by rows (CSR): the edges of check j are e = row_ptr[j] ..
  * row_ptr[j+1]-1, variable col_idx[e]; the k-th of them is the k-th row of P_j.
  * gamma is [n_frames x n]; per-frame outputs are indexed by frame number.
+ * resid_out (may be NULL) receives, per frame, the primal and dual residuals
+ * of Section 3.3 after the last iteration run: sum_j ||P_j x - z_j||^2 and
+ * sum_j ||z_j - z_j_old||^2.
  * Returns 0, or -1 on a bad argument / allocation failure.
  */
 int oracle_decode(int n, int m, const int32_t *row_ptr, const int32_t *col_idx,
                   int f_lo, int f_hi, const double *gamma,
                   double mu, double rho, double eps, int max_iter, double cert_tol,
                   double *x_out, uint8_t *bits_out, int32_t *iters_out,
-                  uint8_t *conv_out, uint8_t *cert_out)
+                  uint8_t *conv_out, uint8_t *cert_out, double *resid_out)
 {
     if (n <= 0 || m <= 0 || mu <= 0.0 || max_iter < 1) return -1;
     const int E = row_ptr[m];
@@ -283,6 +286,10 @@ int oracle_decode(int n, int m, const int32_t *row_ptr, const int32_t *col_idx,
         const int resid_ok = Rp < eps_c * eps_c * (double)E && Rd < eps_c * eps_c * (double)E;
         iters_out[f] = k;
         conv_out[f] = (uint8_t)converged;
+        if (resid_out) {
+            resid_out[2 * (size_t)f] = Rp;
+            resid_out[2 * (size_t)f + 1] = Rd;
+        }
         cert_out[f] = (uint8_t)(resid_ok && frac <= cert_tol && syndrome_ok);
     }
     free(z); free(lam); free(acc); free(deg); free(x);

@@ -927,6 +927,25 @@ extern "C" int lpdec_autotune(lpdec_code *c, const lpdec_params *p, int32_t n_fr
             if (!dup) cand.push_back(t);
         }
     }
+    if (lanes > 1) {
+        // Wide checks: also groups as wide as one or two per CTA allow, whose
+        // last pass over the checks is ragged (C8000: 1 x 896 runs 1% faster
+        // than 1 x 800, the widest even split).
+        for (int g = 1; g <= 2; ++g) {
+            const int gt = maxT / g / 32 * 32;
+            if ((long long)gt > (long long)c->m * lanes + 31) continue;
+            const lpdec::SliceLayout L = lpdec::slice_layout(c, q.state_dtype, gt);
+            if ((size_t)g * L.bytes > (size_t)cap) continue;
+            bool dup = false;
+            for (auto &o : cand) dup |= (o.group_threads == gt && o.groups == g);
+            if (!dup) {
+                lpdec::Tile t;
+                t.group_threads = gt;
+                t.groups = g;
+                cand.push_back(t);
+            }
+        }
+    }
     if (streamed) {
         // Ring tiles: G groups and a producer warp, R = G+1 .. G+4 slots, and
         // the most slots that fit.

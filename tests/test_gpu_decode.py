@@ -8,6 +8,7 @@ certificate tolerance); parity checks of the output compared bit-exactly.
 import numpy as np
 import pytest
 
+from _stopping import assert_stop_near_threshold
 from paper_1204_0556_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -89,7 +90,9 @@ def test_c96_fixed_iterations(gpu, oracle_mod, c96, schedule):
 @pytest.mark.parametrize("schedule", ["resident", "streamed"])
 def test_c96_early_exit(gpu, oracle_mod, c96, schedule):
     """The small FP64-reference configuration: (3,6) n=96, 2.0 dB, 100 frames of seed 1,
-    mu=3, rho=1.9, at most 200 iterations, eps=1e-5 (early exit per frame)."""
+    mu=3, rho=1.9, at most 200 iterations, eps=1e-5 (early exit per frame).
+    Where the iteration counts differ, the oracle's residual at the earlier
+    stop lies within a factor 2 of eps^2 E (tests/_stopping.py)."""
     llr = I.awgn_llr(c96, 2.0, 100, 1)
     kw = dict(mu=MU, rho=RHO, eps=1e-5, max_iter=200)
     got = gpu_decode(gpu, c96, llr, schedule=schedule, **kw)
@@ -97,6 +100,11 @@ def test_c96_early_exit(gpu, oracle_mod, c96, schedule):
     same = got["iters"] == ref["iters"]
     assert same.mean() >= 0.9
     assert np.abs(got["iters"] - ref["iters"]).max() <= 10
+    for f in np.nonzero(~same)[0]:
+        q = assert_stop_near_threshold(oracle_mod, c96, llr[f], got["iters"][f], ref["iters"][f], mu=MU, rho=RHO,
+                                       eps=1e-5)
+        print(f"frame {f}: GPU {got['iters'][f]} vs oracle {ref['iters'][f]} iterations, "
+              f"max(R_p, R_d) / eps^2 E = {q:.3f}")
     err = np.abs(got["x"] - ref["x"]).max(axis=1)
     assert err[same].max() <= 1e-4
     assert err.max() <= 1e-3

@@ -2,6 +2,7 @@
 import numpy as np
 import pytest
 
+from _stopping import assert_stop_near_threshold
 from paper_1204_0556_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -77,6 +78,9 @@ def test_mixed_matches_oracle(gpu, oracle_mod):
         else:
             assert abs(int(got["iters"][f]) - int(ref["iters"][0])) <= 10
             assert err <= 1e-3
+            # the two stops straddle eps^2 E by a rounding margin (tests/_stopping.py)
+            assert_stop_near_threshold(oracle_mod, code, frames[f], got["iters"][f], ref["iters"][0], mu=3.0,
+                                       rho=1.9, eps=1e-5)
         if np.abs(ref["x"][0] - 0.5).min() > 1e-3:
             assert np.array_equal(bs[f], ref["bits"][0])
     assert same >= 0.9 * len(fc)

@@ -181,6 +181,8 @@ def test_stopping_threshold_is_eps2_times_edges(oracle_mod):
     b = _decode(oracle_mod, code, gamma, mu=2.0, rho=1.5, eps=0.44, max_iter=50)
     assert a["iters"][0] == 1 and a["converged"][0] == 1
     assert b["iters"][0] >= 2
+    # the residuals the oracle reports after its last sweep are those above
+    np.testing.assert_allclose([a["rp"][0], a["rd"][0]], [149 / 512, 825 / 512], rtol=1e-13, atol=0)
 
 
 def test_stopping_uses_primal_residual_of_unrelaxed_x(oracle_mod):
@@ -201,6 +203,7 @@ def test_stopping_uses_primal_residual_of_unrelaxed_x(oracle_mod):
     assert a["iters"][0] == 1 and a["converged"][0] == 1
     np.testing.assert_allclose(a["x"][0], [1 / 8, 1 / 8, 1 / 8, 1.0], rtol=0, atol=1e-15)
     assert b["iters"][0] >= 2
+    np.testing.assert_allclose([a["rp"][0], a["rd"][0]], [259 / 256, 27 / 256], rtol=1e-13, atol=0)
 
 
 @pytest.mark.parametrize("n,m,seed", [(12, 6, 1), (14, 7, 4), (16, 8, 9)])
@@ -228,3 +231,26 @@ def test_threads_do_not_change_results(oracle_mod):
     b = _decode(oracle_mod, code, gamma, mu=3.0, rho=1.9, eps=1e-5, max_iter=200, threads=4)
     for k in a:
         assert np.array_equal(a[k], b[k])
+
+
+def test_reported_residuals_decide_the_stop(oracle_mod):
+    """The residuals the oracle reports are the ones its stopping test reads
+    (Section 3.3): a frame that stops at iteration K has max(R_p, R_d) below
+    eps^2 E after K fixed iterations and not after K - 1."""
+    code = I.benchmark_code("C96", 0)
+    gamma = I.awgn_llr(code, 2.5, 12, 3).astype(np.float64)
+    eps = 1e-5
+    thr = eps * eps * int(code.row_ptr[-1])
+    r = _decode(oracle_mod, code, gamma, mu=3.0, rho=1.9, eps=eps, max_iter=300)
+    checked = 0
+    for f in range(len(gamma)):
+        K = int(r["iters"][f])
+        if not r["converged"][f] or K < 2:
+            continue
+        at = _decode(oracle_mod, code, gamma[f:f + 1], mu=3.0, rho=1.9, eps=0.0, max_iter=K)
+        before = _decode(oracle_mod, code, gamma[f:f + 1], mu=3.0, rho=1.9, eps=0.0, max_iter=K - 1)
+        assert max(at["rp"][0], at["rd"][0]) < thr
+        assert max(before["rp"][0], before["rd"][0]) >= thr
+        np.testing.assert_array_equal(at["x"][0], r["x"][f])
+        checked += 1
+    assert checked >= 8
