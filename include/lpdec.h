@@ -305,12 +305,13 @@ LPDEC_API int lpdec_decode_noalloc(const lpdec_code *code, int32_t n_frames, con
  * A continuous-batching decode server on the current device.  Each code added
  * gets a pool of frame slots in device memory (LLRs, outputs and the z/lambda
  * state of frames in flight).  A scheduler thread, started by the first
- * submit, repeats rounds: admit queued frames into free slots, advance every
- * frame in flight by params.iters_per_launch ADMM iterations in one launch per
- * code, and retire frames that converged or reached max_iter (Algorithm 1 per
- * frame, early exit by the stopping test).  Requests that arrive while others
- * are on the GPU join the next round.  A frame's result is identical to
- * lpdec_decode of that frame alone.
+ * submit, runs rounds for each code: admit queued frames into free slots,
+ * advance every frame in flight by params.iters_per_launch ADMM iterations in
+ * one launch, and retire frames that converged or reached max_iter (Algorithm 1
+ * per frame, early exit by the stopping test).  Each code's rounds follow one
+ * another on its own stream without waiting for the other codes' rounds.
+ * Requests that arrive while a code's round is on the GPU join its next round.
+ * A frame's result is identical to lpdec_decode of that frame alone.
  *   device_budget_bytes: upper bound on the device memory of all slot pools.
  *   cuda_stream: work already queued on this stream (NULL: the legacy default
  *                stream) completes before a code's first round; each code's
@@ -350,9 +351,10 @@ LPDEC_API int lpdec_server_poll(lpdec_server *server, uint64_t request_id, int32
 LPDEC_API int lpdec_server_stats(lpdec_server *server, double *p50_ms, double *p99_ms, double *bits_per_s,
                                  int64_t *frames);
 
-/* Scheduler accounting: rounds run, their total host wall time, and their total
- * device time (per round, the slowest code's first-to-last launch span).  Any
- * pointer may be NULL. */
+/* Scheduler accounting: rounds run (of all codes), the host wall time of the
+ * scheduler while a round was in flight, and the device time during which at
+ * least one code's round was running (the union of the rounds' first-launch to
+ * status-copy spans).  Any pointer may be NULL. */
 LPDEC_API int lpdec_server_counters(lpdec_server *server, int64_t *rounds, double *round_wall_ms,
                                     double *round_gpu_ms);
 

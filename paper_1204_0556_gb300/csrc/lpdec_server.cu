@@ -2,17 +2,21 @@
 //
 // Each code added to the server owns a pool of frame slots in device memory:
 // LLRs, x/bits/iteration/certificate outputs and the parked w = z - lambda/mu and lambda/mu
-// state of every frame in flight.  A scheduler thread repeats rounds:
-//   1. admit pending frames (FIFO over requests) into free slots of their
-//      code: one pinned host->device copy of the new LLR rows and a scatter
-//      kernel that places them and marks the slots fresh;
-//   2. advance every active slot of every code by `iters_per_launch` ADMM
-//      iterations with the decode kernel (STREAMED form, indexed by a slot
-//      list): frames admitted this round and frames in flight share the launch,
-//      and each code's launches run on a stream of their own so codes overlap;
-//   3. read back which slots finished (converged or reached max_iter), gather
-//      their outputs into one compact buffer, copy it to the host, free the
-//      slots and complete requests whose frames are all done.
+// state of every frame in flight.  Each code runs its own rounds, on a stream
+// of its own, and a scheduler thread keeps every code's rounds going:
+//   1. for a code with no round in flight, admit pending frames (FIFO over
+//      requests) into free slots: one pinned host->device copy of the new LLR
+//      rows and a scatter kernel that places them and marks the slots fresh;
+//   2. launch the code's round: advance every active slot by `iters_per_launch`
+//      ADMM iterations with the decode kernel (STREAMED form, indexed by a slot
+//      list), then copy back which slots finished (converged or reached
+//      max_iter);
+//   3. when a code's round completes, gather the outputs of its finished slots
+//      into one compact buffer, copy it to the host, free the slots, complete
+//      requests whose frames are all done, and start the code's next round.
+// The codes' rounds do not wait for one another: a code with long frames
+// (many iterations, many edges) does not hold back the others, and its own
+// rounds follow each other with only its own bookkeeping in between.
 // A frame's arithmetic depends only on its own state, and the kernel runs the
 // same iterations whatever the round boundaries, so a result is identical
 // whether the frame was decoded alone or among others.
@@ -111,11 +115,22 @@ struct Pool {
     std::deque<Request *> pending;
     int n_new = 0;
     cudaStream_t stream = nullptr;  // this code's rounds run here, overlapping the other codes
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    bool timed = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // a round's first launch; its status copy
+    bool in_flight = false;                    // a round is queued; active is the list it runs on
 };
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Merge device-time intervals into disjoint ones (their union is unchanged).
+void merge_intervals(std::vector<std::pair<float, float>> &v) {
+    std::sort(v.begin(), v.end());
+    size_t k = 0;
+    for (size_t i = 0; i < v.size(); ++i) {
+        if (k > 0 && v[i].first <= v[k - 1].second) v[k - 1].second = std::max(v[k - 1].second, v[i].second);
+        else v[k++] = v[i];
+    }
+    v.resize(k);
+}
 
 }  // namespace
 }  // namespace lpdec
@@ -143,9 +158,10 @@ struct lpdec_server {
     lpdec::Clock::time_point t_first, t_last;
     bool have_first = false;
     // round accounting
-    int64_t rounds = 0;
-    double round_wall_ms = 0.0;  // host time of whole rounds
-    double round_gpu_ms = 0.0;   // device time of a round: its slowest code, first launch to last
+    int64_t rounds = 0;          // rounds of all codes
+    double round_wall_ms = 0.0;  // host time of scheduler steps that had a round in flight
+    cudaEvent_t ev_ref = nullptr;                 // device-time origin of the busy intervals
+    std::vector<std::pair<float, float>> busy;    // device intervals [ms] of the rounds, merged as they grow
 };
 
 namespace lpdec {
@@ -231,107 +247,95 @@ int pool_alloc(lpdec_server *sv, Pool &P, int slots) {
     return LPDEC_OK;
 }
 
-// One scheduling round.  Returns an LPDEC status; the caller holds no lock.
-// lpdec_server_add_code may append to sv->pools at any time (under the lock),
-// so the round works on a copy of the pool pointers taken under the lock in
-// step 1; the Pool objects themselves never move.  A code added meanwhile
-// joins the next round.
-int run_round(lpdec_server *sv) {
-    const auto t_round = Clock::now();
-    std::vector<Pool *> pools;
-    // ---- 1. admission (under the lock)
-    {
-        std::lock_guard<std::mutex> lk(sv->mu);
-        pools.reserve(sv->pools.size());
-        for (auto &pp : sv->pools) pools.push_back(pp.get());
-        for (Pool *pp : pools) {
-            Pool &P = *pp;
-            P.n_new = 0;
-            const int n = P.code->n;
-            while (!P.pending.empty() && !P.free_slots.empty()) {
-                Request *r = P.pending.front();
-                while (r->next_frame < r->n_frames && !P.free_slots.empty()) {
-                    const int s = P.free_slots.back();
-                    P.free_slots.pop_back();
-                    std::memcpy(P.h_new_llr + (size_t)P.n_new * n, r->llr.data() + (size_t)r->next_frame * n,
-                                (size_t)n * 4);
-                    P.h_new_slots[P.n_new++] = s;
-                    P.owner[s] = {r, r->next_frame};
-                    P.active.push_back(s);
-                    ++r->next_frame;
-                    --sv->pending_frames;
-                }
-                if (r->next_frame == r->n_frames) P.pending.pop_front();
-            }
+// Admission for a code with no round in flight (the caller holds the lock).
+void admit_locked(lpdec_server *sv, Pool &P) {
+    P.n_new = 0;
+    const int n = P.code->n;
+    while (!P.pending.empty() && !P.free_slots.empty()) {
+        Request *r = P.pending.front();
+        while (r->next_frame < r->n_frames && !P.free_slots.empty()) {
+            const int s = P.free_slots.back();
+            P.free_slots.pop_back();
+            std::memcpy(P.h_new_llr + (size_t)P.n_new * n, r->llr.data() + (size_t)r->next_frame * n, (size_t)n * 4);
+            P.h_new_slots[P.n_new++] = s;
+            P.owner[s] = {r, r->next_frame};
+            P.active.push_back(s);
+            ++r->next_frame;
+            --sv->pending_frames;
         }
+        if (r->next_frame == r->n_frames) P.pending.pop_front();
     }
-    // ---- 2. device work for every pool with frames in flight, each on its own
-    // stream so the codes' launches overlap
+}
+
+// Queue one round of a code on its stream (no lock held; the scheduler thread
+// alone touches a pool's device buffers and its active list while in flight).
+int launch_round(lpdec_server *sv, Pool &P) {
+    cudaStream_t st = P.stream;
     cudaError_t err;
-    for (Pool *pp : pools) {
-        Pool &P = *pp;
-        P.timed = false;
-        if (P.active.empty()) continue;
-        cudaStream_t st = P.stream;
-        cudaEventRecord(P.ev0, st);
-        P.timed = true;
-        const int n = P.code->n;
-        if (P.n_new > 0) {
-            err = cudaMemcpyAsync(P.d_new_llr, P.h_new_llr, (size_t)P.n_new * n * 4, cudaMemcpyHostToDevice, st);
-            if (err == cudaSuccess)
-                err = cudaMemcpyAsync(P.d_new_slots, P.h_new_slots, (size_t)P.n_new * 4, cudaMemcpyHostToDevice, st);
-            if (err != cudaSuccess) return cuda_error(err, "server: admission copy");
-            scatter_new_frames<<<P.n_new, 128, 0, st>>>(n, P.n_new, P.d_new_slots, P.d_new_llr, P.llr, P.kst);
-        }
-        const int na = (int)P.active.size();
-        std::memcpy(P.h_active, P.active.data(), (size_t)na * 4);
-        err = cudaMemcpyAsync(P.d_active, P.h_active, (size_t)na * 4, cudaMemcpyHostToDevice, st);
-        if (err == cudaSuccess) err = cudaMemsetAsync(P.d_queue, 0, 4, st);
-        if (err != cudaSuccess) return cuda_error(err, "server: round set-up");
-        DecodeArgs a;
-        std::memset(&a, 0, sizeof(a));
-        a.code = make_view(P.code);
-        a.cfg = make_cfg(P.code, &P.params);
-        a.n_frames = na;
-        a.llr = P.llr;
-        a.x_out = P.x;
-        a.bits_out = P.bits;
-        a.iters_out = P.iters;
-        a.cert_out = P.cert;
-        a.w_state = P.wst;
-        a.l_state = P.lst;
-        a.k_state = P.kst;
-        a.iters_this_launch = P.params.iters_per_launch;
-        a.frame_list = P.d_active;
-        a.queue = P.d_queue;
-        int rc = launch_once(P.code, P.params.state_dtype, P.tile, a, st);
-        if (rc) return rc;
-        gather_k_state<<<(na + 255) / 256, 256, 0, st>>>(na, P.d_active, P.kst, P.d_kc);
-        cudaEventRecord(P.ev1, st);
-        err = cudaMemcpyAsync(P.h_kc, P.d_kc, (size_t)na * 4, cudaMemcpyDeviceToHost, st);
-        if (err != cudaSuccess) return cuda_error(err, "server: status copy");
+    if (!sv->ev_ref) {
+        // the origin of the busy intervals, recorded on a stream of its own so
+        // that it completes at once (the code streams may wait on the caller's work)
+        cudaStream_t s0 = nullptr;
+        err = cudaEventCreate(&sv->ev_ref);
+        if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&s0, cudaStreamNonBlocking);
+        if (err == cudaSuccess) err = cudaEventRecord(sv->ev_ref, s0);
+        if (err == cudaSuccess) err = cudaEventSynchronize(sv->ev_ref);
+        if (s0) cudaStreamDestroy(s0);
+        if (err != cudaSuccess) return cuda_error(err, "server: reference event");
     }
-    float gpu_ms = 0.0f;
-    for (Pool *pp : pools) {
-        Pool &P = *pp;
-        if (!P.timed) continue;
-        err = cudaStreamSynchronize(P.stream);
-        if (err != cudaSuccess) return cuda_error(err, "server: round");
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, P.ev0, P.ev1);
-        gpu_ms = std::max(gpu_ms, ms);  // the codes overlap: the round takes its slowest code
+    cudaEventRecord(P.ev0, st);
+    const int n = P.code->n;
+    if (P.n_new > 0) {
+        err = cudaMemcpyAsync(P.d_new_llr, P.h_new_llr, (size_t)P.n_new * n * 4, cudaMemcpyHostToDevice, st);
+        if (err == cudaSuccess)
+            err = cudaMemcpyAsync(P.d_new_slots, P.h_new_slots, (size_t)P.n_new * 4, cudaMemcpyHostToDevice, st);
+        if (err != cudaSuccess) return cuda_error(err, "server: admission copy");
+        scatter_new_frames<<<P.n_new, 128, 0, st>>>(n, P.n_new, P.d_new_slots, P.d_new_llr, P.llr, P.kst);
     }
-    // ---- 3. finished frames: gather and copy their outputs
-    std::vector<int> nfin(pools.size(), 0);
-    for (size_t pi = 0; pi < pools.size(); ++pi) {
-        Pool &P = *pools[pi];
-        const int na = (int)P.active.size();
-        int nf = 0;
-        for (int i = 0; i < na; ++i)
-            if (P.h_kc[i] < 0) P.h_fin[nf++] = P.active[i];
-        nfin[pi] = nf;
-        if (!nf) continue;
-        const int n = P.code->n;
+    const int na = (int)P.active.size();
+    std::memcpy(P.h_active, P.active.data(), (size_t)na * 4);
+    err = cudaMemcpyAsync(P.d_active, P.h_active, (size_t)na * 4, cudaMemcpyHostToDevice, st);
+    if (err == cudaSuccess) err = cudaMemsetAsync(P.d_queue, 0, 4, st);
+    if (err != cudaSuccess) return cuda_error(err, "server: round set-up");
+    DecodeArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.code = make_view(P.code);
+    a.cfg = make_cfg(P.code, &P.params);
+    a.n_frames = na;
+    a.llr = P.llr;
+    a.x_out = P.x;
+    a.bits_out = P.bits;
+    a.iters_out = P.iters;
+    a.cert_out = P.cert;
+    a.w_state = P.wst;
+    a.l_state = P.lst;
+    a.k_state = P.kst;
+    a.iters_this_launch = P.params.iters_per_launch;
+    a.frame_list = P.d_active;
+    a.queue = P.d_queue;
+    int rc = launch_once(P.code, P.params.state_dtype, P.tile, a, st);
+    if (rc) return rc;
+    gather_k_state<<<(na + 255) / 256, 256, 0, st>>>(na, P.d_active, P.kst, P.d_kc);
+    err = cudaMemcpyAsync(P.h_kc, P.d_kc, (size_t)na * 4, cudaMemcpyDeviceToHost, st);
+    if (err == cudaSuccess) err = cudaEventRecord(P.ev1, st);
+    if (err != cudaSuccess) return cuda_error(err, "server: status copy");
+    P.in_flight = true;
+    return LPDEC_OK;
+}
+
+// A code's round has completed (ev1 reached): retire its finished slots and
+// hand their outputs to their requests.
+int finish_round(lpdec_server *sv, Pool &P) {
+    cudaError_t err;
+    float t0 = 0.0f, t1 = 0.0f;
+    const bool timed = cudaEventElapsedTime(&t0, sv->ev_ref, P.ev0) == cudaSuccess &&
+                       cudaEventElapsedTime(&t1, sv->ev_ref, P.ev1) == cudaSuccess;
+    const int na = (int)P.active.size();
+    int nf = 0;
+    for (int i = 0; i < na; ++i)
+        if (P.h_kc[i] < 0) P.h_fin[nf++] = P.active[i];
+    const int n = P.code->n;
+    if (nf) {
         cudaStream_t st = P.stream;
         err = cudaMemcpyAsync(P.d_fin, P.h_fin, (size_t)nf * 4, cudaMemcpyHostToDevice, st);
         if (err != cudaSuccess) return cuda_error(err, "server: finished list copy");
@@ -341,55 +345,98 @@ int run_round(lpdec_server *sv) {
         if (err == cudaSuccess) err = cudaMemcpyAsync(P.h_bo, P.d_bo, (size_t)nf * n, cudaMemcpyDeviceToHost, st);
         if (err == cudaSuccess) err = cudaMemcpyAsync(P.h_io, P.d_io, (size_t)nf * 4, cudaMemcpyDeviceToHost, st);
         if (err == cudaSuccess) err = cudaMemcpyAsync(P.h_co, P.d_co, (size_t)nf, cudaMemcpyDeviceToHost, st);
-        if (err != cudaSuccess) return cuda_error(err, "server: output copy");
-    }
-    for (size_t pi = 0; pi < pools.size(); ++pi) {
-        if (!nfin[pi]) continue;
-        err = cudaStreamSynchronize(pools[pi]->stream);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(st);
         if (err != cudaSuccess) return cuda_error(err, "server: output gather");
     }
-    // ---- 4. hand results to their requests (under the lock)
+    std::lock_guard<std::mutex> lk(sv->mu);
+    const auto now = Clock::now();
+    bool any_done = false;
+    for (int i = 0; i < nf; ++i) {
+        const int s = P.h_fin[i];
+        Request *r = P.owner[s].first;
+        const int fr = P.owner[s].second;
+        std::memcpy(r->x.data() + (size_t)fr * n, P.h_xo + (size_t)i * n, (size_t)n * 4);
+        std::memcpy(r->bits.data() + (size_t)fr * n, P.h_bo + (size_t)i * n, (size_t)n);
+        r->iters[fr] = P.h_io[i];
+        r->cert[fr] = P.h_co[i];
+        P.owner[s] = {nullptr, 0};
+        P.free_slots.push_back(s);
+        if (++r->done_frames == r->n_frames) {
+            r->done = true;
+            any_done = true;
+            const double ms = std::chrono::duration<double, std::milli>(now - r->t_submit).count();
+            sv->lat_ms.push_back(ms);
+            sv->frames_done += r->n_frames;
+            sv->info_bits += (double)r->n_frames * (P.code->n - P.code->m);
+            sv->t_last = now;
+        }
+    }
+    if (nf) {  // drop finished slots from the active list
+        std::vector<int> keep;
+        keep.reserve(P.active.size());
+        for (int i = 0; i < na; ++i)
+            if (P.h_kc[i] >= 0) keep.push_back(P.active[i]);
+        P.active.swap(keep);
+    }
+    P.in_flight = false;
+    if (any_done) sv->cv_done.notify_all();
+    sv->rounds += 1;
+    if (timed) sv->busy.emplace_back(t0, t1);
+    if (sv->busy.size() >= 4096) merge_intervals(sv->busy);
+    return LPDEC_OK;
+}
+
+// One scheduler step: start a round for every code that has none in flight and
+// has frames to run, then wait until some round completes (or new frames
+// arrive for an idle code) and retire the completed rounds.  Returns an LPDEC
+// status; the caller holds no lock.  lpdec_server_add_code may append to
+// sv->pools at any time (under the lock), so the step works on a copy of the
+// pool pointers taken under the lock; the Pool objects themselves never move.
+int run_step(lpdec_server *sv) {
+    const auto t_step = Clock::now();
+    std::vector<Pool *> pools, start;
     {
         std::lock_guard<std::mutex> lk(sv->mu);
-        const auto now = Clock::now();
-        bool any_done = false;
-        for (size_t pi = 0; pi < pools.size(); ++pi) {
-            Pool &P = *pools[pi];
-            const int nf = nfin[pi];
-            if (!nf) continue;
-            const int n = P.code->n;
-            for (int i = 0; i < nf; ++i) {
-                const int s = P.h_fin[i];
-                Request *r = P.owner[s].first;
-                const int fr = P.owner[s].second;
-                std::memcpy(r->x.data() + (size_t)fr * n, P.h_xo + (size_t)i * n, (size_t)n * 4);
-                std::memcpy(r->bits.data() + (size_t)fr * n, P.h_bo + (size_t)i * n, (size_t)n);
-                r->iters[fr] = P.h_io[i];
-                r->cert[fr] = P.h_co[i];
-                P.owner[s] = {nullptr, 0};
-                P.free_slots.push_back(s);
-                if (++r->done_frames == r->n_frames) {
-                    r->done = true;
-                    any_done = true;
-                    const double ms = std::chrono::duration<double, std::milli>(now - r->t_submit).count();
-                    sv->lat_ms.push_back(ms);
-                    sv->frames_done += r->n_frames;
-                    sv->info_bits += (double)r->n_frames * (P.code->n - P.code->m);
-                    sv->t_last = now;
-                }
-            }
-            // drop finished slots from the active list
-            std::vector<int> keep;
-            keep.reserve(P.active.size());
-            for (size_t i = 0; i < P.active.size(); ++i)
-                if (P.h_kc[i] >= 0) keep.push_back(P.active[i]);
-            P.active.swap(keep);
+        pools.reserve(sv->pools.size());
+        for (auto &pp : sv->pools) pools.push_back(pp.get());
+        for (Pool *pp : pools) {
+            if (pp->in_flight) continue;
+            admit_locked(sv, *pp);
+            if (!pp->active.empty()) start.push_back(pp);
         }
-        if (any_done) sv->cv_done.notify_all();
-        sv->rounds += 1;
-        sv->round_gpu_ms += gpu_ms;
-        sv->round_wall_ms += std::chrono::duration<double, std::milli>(Clock::now() - t_round).count();
     }
+    for (Pool *pp : start) {
+        const int rc = launch_round(sv, *pp);
+        if (rc) return rc;
+    }
+    bool any_flight = false;
+    for (Pool *pp : pools) any_flight |= pp->in_flight;
+    if (!any_flight) return LPDEC_OK;
+    // wait for a completed round, or for frames that an idle code could start on
+    std::vector<Pool *> done;
+    for (;;) {
+        for (Pool *pp : pools) {
+            if (!pp->in_flight) continue;
+            const cudaError_t q = cudaEventQuery(pp->ev1);
+            if (q == cudaSuccess) done.push_back(pp);
+            else if (q != cudaErrorNotReady) return cuda_error(q, "server: round");
+        }
+        if (!done.empty()) break;
+        bool idle_work = false;
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            for (Pool *pp : pools)
+                if (!pp->in_flight && !pp->pending.empty() && !pp->free_slots.empty()) idle_work = true;
+        }
+        if (idle_work) break;
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    for (Pool *pp : done) {
+        const int rc = finish_round(sv, *pp);
+        if (rc) return rc;
+    }
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->round_wall_ms += std::chrono::duration<double, std::milli>(Clock::now() - t_step).count();
     return LPDEC_OK;
 }
 
@@ -409,7 +456,7 @@ void worker_main(lpdec_server *sv) {
                 if (!pp->active.empty() || !pp->pending.empty()) busy = true;
             if (sv->stop && !busy) return;
         }
-        const int rc = run_round(sv);
+        const int rc = run_step(sv);
         if (rc) {
             std::lock_guard<std::mutex> lk(sv->mu);
             sv->failed = rc;
@@ -579,7 +626,12 @@ extern "C" int lpdec_server_counters(lpdec_server *sv, int64_t *rounds, double *
     std::lock_guard<std::mutex> lk(sv->mu);
     if (rounds) *rounds = sv->rounds;
     if (round_wall_ms) *round_wall_ms = sv->round_wall_ms;
-    if (round_gpu_ms) *round_gpu_ms = sv->round_gpu_ms;
+    if (round_gpu_ms) {
+        lpdec::merge_intervals(sv->busy);
+        double ms = 0.0;
+        for (const auto &iv : sv->busy) ms += (double)(iv.second - iv.first);
+        *round_gpu_ms = ms;
+    }
     return LPDEC_OK;
 }
 
@@ -601,6 +653,7 @@ extern "C" int lpdec_server_destroy(lpdec_server *sv) {
         if (pp->ev1) cudaEventDestroy(pp->ev1);
         if (pp->stream) cudaStreamDestroy(pp->stream);
     }
+    if (sv->ev_ref) cudaEventDestroy(sv->ev_ref);
     if (sv->own_stream) cudaStreamDestroy(sv->stream);
     delete sv;
     if (rc) return set_error(rc, "lpdec_server_destroy: freeing device memory failed");
