@@ -506,44 +506,68 @@ def run_served(args):
     import ctypes
 
     rid_c = ctypes.c_uint64()
+    # Warm start: a code's first request sizes and allocates its slot pool (a
+    # one-time set-up of the server, hundreds of MB of device and pinned host
+    # memory); one request per code is served before the timed stream.
+    for c in range(4):
+        st = sub_fn(srv.handle, ids[c], 1, ptrs[c][POOL - 1], ctypes.byref(p), ctypes.byref(rid_c))
+        if st == 0:
+            st = poll_fn(srv.handle, int(rid_c.value), -1, outx[c].ctypes.data, outb[c].ctypes.data,
+                         it_buf.ctypes.data, ce_buf.ctypes.data)
+        if st != 0:
+            raise RuntimeError(lpdec.lpdec_last_error())
     done_submit = threading.Event()
     submitted = [0]
     busy_waits = [0]
+
+    # Everything a submit needs is prepared before the timed stream, so that the
+    # Python submit loop does as little as it can per request.
+    req_code = [int(c) for c in which]
+    req_ptr = []
+    for c in req_code:
+        req_ptr.append(ptrs[c][cursor[c]])
+        cursor[c] = (cursor[c] + 1) % POOL
+    req_id = [ids[c] for c in req_code]
+    arr = arrivals.tolist()
+    rid_l = [0] * R
+    lag_l = [0.0] * R
+    h, p_ref, rid_ref, pc = srv.handle, ctypes.byref(p), ctypes.byref(rid_c), time.perf_counter
+    x_ptr = [o.ctypes.data for o in outx]
+    b_ptr = [o.ctypes.data for o in outb]
+    it_ptr, ce_ptr = it_buf.ctypes.data, ce_buf.ctypes.data
 
     def poller():
         for i in range(R):
             while submitted[0] <= i:
                 time.sleep(0.0002)
-            c = which[i]
-            st = poll_fn(srv.handle, int(rid[i]), -1, outx[c].ctypes.data, outb[c].ctypes.data, it_buf.ctypes.data,
-                         ce_buf.ctypes.data)
-            if st != 0:
+            c = req_code[i]
+            if poll_fn(h, rid_l[i], -1, x_ptr[c], b_ptr[c], it_ptr, ce_ptr) != 0:
                 raise RuntimeError(lpdec.lpdec_last_error())
             iters[i] = it_buf[0]
             err[i] = bool(outb[c].any())
 
     th = threading.Thread(target=poller)
     th.start()
-    t0 = time.perf_counter()
+    t0 = pc()
     for i in range(R):
-        while time.perf_counter() - t0 < arrivals[i]:
+        a = arr[i]
+        while pc() - t0 < a:
             pass
-        c = which[i]
-        k = cursor[c]
-        cursor[c] = (k + 1) % POOL
-        st = sub_fn(srv.handle, ids[c], 1, ptrs[c][k], ctypes.byref(p), ctypes.byref(rid_c))
+        st = sub_fn(h, req_id[i], 1, req_ptr[i], p_ref, rid_ref)
         while st == lpdec.LPDEC_EBUSY:  # back-pressure: the queue is full, wait for the server
             busy_waits[0] += 1
             time.sleep(0.0005)
-            st = sub_fn(srv.handle, ids[c], 1, ptrs[c][k], ctypes.byref(p), ctypes.byref(rid_c))
+            st = sub_fn(h, req_id[i], 1, req_ptr[i], p_ref, rid_ref)
         if st != 0:
             raise RuntimeError(lpdec.lpdec_last_error())
-        rid[i] = rid_c.value
-        submit_lag[i] = (time.perf_counter() - t0) - arrivals[i]
+        rid_l[i] = rid_c.value
+        lag_l[i] = pc() - t0 - a
         submitted[0] = i + 1
     done_submit.set()
     th.join()
-    wall = time.perf_counter() - t0
+    wall = pc() - t0
+    rid[:] = rid_l
+    submit_lag[:] = lag_l
     st = srv.stats()
     ctr = srv.counters()
     srv.close()
@@ -567,8 +591,10 @@ def run_served(args):
                                               "frames": 4 * POOL}
     line = {
         "workload": "served", "metric": "ADMM-LP served decode stream: sustained info bits/s, p50/p99 latency",
-        "unit": UNIT, "value": st["bits_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-        "frames": int(st["frames"]), "wall_s": wall, "info_bits_per_s_wall": info / wall,
+        "unit": UNIT, "value": info / wall, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+        "frames": R, "wall_s": wall, "server_bits_per_s_since_first_submit": st["bits_per_s"],
+        "value_note": "info bits of the timed requests over the wall time from the first timed submit to the last "
+                      "completion (bench clock), after one warm-up request per code",
         "offered_frames_per_s": args.served_rate, "achieved_submit_frames_per_s": R / (arrivals[-1] + submit_lag[-1]),
         "submit_lag_ms_p50": float(np.quantile(submit_lag, 0.50) * 1000),
         "submit_lag_ms_p99": float(np.quantile(submit_lag, 0.99) * 1000),
@@ -612,6 +638,10 @@ def served_latency(lpdec, C, code, llr_h, rate: float, seconds: float, round_ite
     rid_c = ctypes.c_uint64()
     submitted = [0]
     outx = np.empty(code.n, np.float32)
+    # warm start: the first request allocates the code's slot pool (one-time set-up)
+    if sub_fn(srv.handle, cid, 1, ptrs[0], ctypes.byref(p), ctypes.byref(rid_c)) != 0 or \
+            poll_fn(srv.handle, int(rid_c.value), -1, outx.ctypes.data, None, None, None) != 0:
+        raise RuntimeError(lpdec.lpdec_last_error())
 
     def poller():
         for i in range(R):
@@ -635,10 +665,11 @@ def served_latency(lpdec, C, code, llr_h, rate: float, seconds: float, round_ite
         rid[i] = rid_c.value
         submitted[0] = i + 1
     th.join()
+    wall = time.perf_counter() - t0
     stats = srv.stats()
     srv.close()
-    return {"p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"], "sustained_bits_per_s": stats["bits_per_s"],
-            "offered_frames_per_s": rate, "frames": int(stats["frames"]), "iters_per_round": round_iters,
+    return {"p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"], "sustained_bits_per_s": R * code.k_design / wall,
+            "offered_frames_per_s": rate, "frames": R, "iters_per_round": round_iters,
             "note": f"the headline's C1056 frames and parameters ({ITERS} fixed iterations, FP32) as Poisson "
                     "one-frame requests through lpdec_server; latency from submit to completion"}
 

@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -117,6 +118,8 @@ struct Pool {
     cudaStream_t stream = nullptr;  // this code's rounds run here, overlapping the other codes
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // a round's first launch; its status copy
     bool in_flight = false;                    // a round is queued; active is the list it runs on
+    std::atomic<int> queued{0};  // frames in pending (read without the lock by the scheduler's wait)
+    float last_end = -1e30f;     // device time [ms] at which this code's last completed round ended
 };
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -161,7 +164,9 @@ struct lpdec_server {
     int64_t rounds = 0;          // rounds of all codes
     double round_wall_ms = 0.0;  // host time of scheduler steps that had a round in flight
     cudaEvent_t ev_ref = nullptr;                 // device-time origin of the busy intervals
-    std::vector<std::pair<float, float>> busy;    // device intervals [ms] of the rounds, merged as they grow
+    std::vector<std::pair<float, float>> busy;    // device intervals [ms] of recent rounds
+    double busy_settled_ms = 0.0;                 // union length of older rounds, which no later round overlaps
+    size_t busy_merge_at = 256;                   // merge when busy reaches this size (doubling: amortized cost)
 };
 
 namespace lpdec {
@@ -262,6 +267,7 @@ void admit_locked(lpdec_server *sv, Pool &P) {
             P.active.push_back(s);
             ++r->next_frame;
             --sv->pending_frames;
+            P.queued.fetch_sub(1, std::memory_order_relaxed);
         }
         if (r->next_frame == r->n_frames) P.pending.pop_front();
     }
@@ -381,8 +387,27 @@ int finish_round(lpdec_server *sv, Pool &P) {
     P.in_flight = false;
     if (any_done) sv->cv_done.notify_all();
     sv->rounds += 1;
-    if (timed) sv->busy.emplace_back(t0, t1);
-    if (sv->busy.size() >= 4096) merge_intervals(sv->busy);
+    if (timed) {
+        sv->busy.emplace_back(t0, t1);
+        P.last_end = t1;
+    }
+    if (sv->busy.size() >= sv->busy_merge_at) {
+        // A round not yet completed runs on its code's stream after that code's
+        // last completed round, and a round launched later starts later still:
+        // no future interval begins before the earliest last_end of the codes
+        // in flight.  The merged intervals that end before it are settled.
+        merge_intervals(sv->busy);
+        float horizon = 1e30f;
+        for (auto &pp : sv->pools)
+            if (pp->in_flight) horizon = std::min(horizon, pp->last_end);
+        size_t k = 0;
+        while (k < sv->busy.size() && sv->busy[k].second <= horizon) {
+            sv->busy_settled_ms += (double)(sv->busy[k].second - sv->busy[k].first);
+            ++k;
+        }
+        sv->busy.erase(sv->busy.begin(), sv->busy.begin() + (long)k);
+        sv->busy_merge_at = std::max<size_t>(256, 2 * sv->busy.size());
+    }
     return LPDEC_OK;
 }
 
@@ -422,14 +447,18 @@ int run_step(lpdec_server *sv) {
             else if (q != cudaErrorNotReady) return cuda_error(q, "server: round");
         }
         if (!done.empty()) break;
+        // (without the lock, which the submitting threads need: in_flight
+        // changes only on this thread, queued is atomic, and free_slots, sized
+        // by the code's first submit before it raises queued, changes only on
+        // this thread afterwards)
         bool idle_work = false;
-        {
-            std::lock_guard<std::mutex> lk(sv->mu);
-            for (Pool *pp : pools)
-                if (!pp->in_flight && !pp->pending.empty() && !pp->free_slots.empty()) idle_work = true;
-        }
+        for (Pool *pp : pools)
+            if (!pp->in_flight && pp->queued.load(std::memory_order_acquire) > 0 && !pp->free_slots.empty())
+                idle_work = true;
         if (idle_work) break;
-        std::this_thread::sleep_for(std::chrono::microseconds(20));
+        // spin (yielding the core): a sleep of even 20 us measurably delays
+        // every round of a code whose rounds are short
+        std::this_thread::yield();
     }
     for (Pool *pp : done) {
         const int rc = finish_round(sv, *pp);
@@ -564,6 +593,7 @@ extern "C" int lpdec_server_submit(lpdec_server *sv, int32_t code_id, int32_t n_
         sv->have_first = true;
     }
     P.pending.push_back(r.get());
+    P.queued.fetch_add(n_frames, std::memory_order_release);  // after the pool's first sizing
     sv->pending_frames += n_frames;
     *request_id = r->id;
     sv->reqs.emplace(r->id, std::move(r));
@@ -628,7 +658,7 @@ extern "C" int lpdec_server_counters(lpdec_server *sv, int64_t *rounds, double *
     if (round_wall_ms) *round_wall_ms = sv->round_wall_ms;
     if (round_gpu_ms) {
         lpdec::merge_intervals(sv->busy);
-        double ms = 0.0;
+        double ms = sv->busy_settled_ms;
         for (const auto &iv : sv->busy) ms += (double)(iv.second - iv.first);
         *round_gpu_ms = ms;
     }
