@@ -27,6 +27,7 @@ def test_results_identical_alone_and_in_the_mix(gpu, server_codes):
     codes, handles = server_codes
     p = gpu.make_params(mu=3.0, rho=1.9, eps=1e-5, max_iter=600, iters_per_launch=8)
     srv = gpu.Server(budget_bytes=2 << 30)
+    t0 = time.perf_counter()
     try:
         ids = [srv.add_code(h) for h in handles]
         rng = np.random.default_rng(9)
@@ -40,10 +41,16 @@ def test_results_identical_alone_and_in_the_mix(gpu, server_codes):
                 time.sleep(0.002)  # let rounds start while more requests arrive
         results = [srv.poll(rid, ids[c], len(llr), timeout_ms=60_000) for c, llr, rid in plan]
         st = srv.stats()
+        ctr = srv.counters()
+        wall_ms = (time.perf_counter() - t0) * 1000.0
     finally:
         srv.close()
     assert st["frames"] == sum(len(llr) for _, llr, _ in plan)
     assert st["p99_ms"] >= st["p50_ms"] > 0
+    # every code ran rounds of its own; the device-busy time is the union of
+    # the rounds' spans, so it lies within the wall time
+    assert ctr["rounds"] >= 4
+    assert 0 < ctr["round_gpu_ms"] <= wall_ms
     for (c, llr, _), got in zip(plan, results):
         assert got is not None
         ref = gpu_decode(gpu, codes[c], llr, mu=3.0, rho=1.9, eps=1e-5, max_iter=600)
