@@ -108,3 +108,69 @@ def test_mixed_rejects_bad_arguments(gpu):
             gpu.decode_mixed([C], [0], llr, gpu.make_params(schedule="streamed"))
     finally:
         C.close()
+
+
+def test_mixed_full_bench_size(gpu, oracle_mod):
+    """`bench.py --workload mixed` at full size, in the bench's launch
+    configuration: 3 x 10^4 frames of C1056 / C2640 / C4000 (12000 / 12000 /
+    6000, shuffled by Philox key 3), Eb/N0 ~ U[1.5, 4.0] dB per frame (key 4),
+    LLR seeds 40 + code, eps = 1e-5, at most 1000 iterations, every code's tile
+    autotuned as the bench does.  Every frame of the one launch equals the
+    per-code decode of the same frame bit for bit, and sampled frames of each
+    code match the oracle (x within 1e-4 where the iteration counts agree, and
+    any other count explained by the stopping threshold)."""
+    import torch
+
+    codes = [I.benchmark_code("C1056", 0), I.benchmark_code("C2640", 1), I.benchmark_code("C4000", 2)]
+    F = 30_000
+    counts = [int(0.4 * F), int(0.4 * F), F - 2 * int(0.4 * F)]
+    order = np.random.Generator(np.random.Philox(key=3)).permutation(F)
+    fc = np.concatenate([np.full(n, c, dtype=np.int32) for c, n in enumerate(counts)])[order]
+    snr = np.random.Generator(np.random.Philox(key=4)).uniform(1.5, 4.0, F)
+    per = {}
+    for c, code in enumerate(codes):
+        idx = np.nonzero(fc == c)[0]
+        per[c] = (idx, I.awgn_llr(code, snr[idx], len(idx), 40 + c))
+    offsets = np.concatenate([[0], np.cumsum([codes[c].n for c in fc])])
+    packed = np.empty(offsets[-1], dtype=np.float32)
+    for c, (idx, llr) in per.items():
+        for r, f in enumerate(idx):
+            packed[offsets[f]:offsets[f + 1]] = llr[r]
+    kw = dict(mu=3.0, rho=1.9, eps=1e-5, max_iter=1000)
+    p = gpu.make_params(state="f32", schedule="resident", **kw)
+    Cs = [gpu.Code(cd) for cd in codes]
+    try:
+        stream = int(torch.cuda.current_stream().cuda_stream)
+        for c, C in enumerate(Cs):  # the bench's autotuning: up to 16384 frames, 60 fixed iterations
+            sample = torch.from_numpy(np.ascontiguousarray(per[c][1][:16384])).cuda()
+            gpu.lpdec_autotune(C.handle, gpu.make_params(mu=3.0, rho=1.9, eps=0.0, max_iter=60, state="f32",
+                                                         schedule="resident"),
+                               sample.shape[0], sample.data_ptr(), stream)
+        out = gpu.decode_mixed(Cs, fc, torch.from_numpy(packed).cuda(), p)
+        got = {k: v.cpu().numpy() for k, v in out.items()}
+        alone = {c: {k: v.cpu().numpy() for k, v in gpu.decode(Cs[c], torch.from_numpy(llr).cuda(), p).items()}
+                 for c, (idx, llr) in per.items()}
+    finally:
+        for C in Cs:
+            C.close()
+    for c, (idx, llr) in per.items():
+        n = codes[c].n
+        x = np.stack([got["x"][offsets[f]:offsets[f + 1]] for f in idx])
+        b = np.stack([got["bits"][offsets[f]:offsets[f + 1]] for f in idx])
+        assert np.array_equal(x, alone[c]["x"].reshape(len(idx), n)), codes[c].name
+        assert np.array_equal(b, alone[c]["bits"].reshape(len(idx), n)), codes[c].name
+        assert np.array_equal(got["iters"][idx], alone[c]["iters"]), codes[c].name
+        assert np.array_equal(got["cert"][idx], alone[c]["cert"]), codes[c].name
+    rng = np.random.default_rng(31)
+    for c, (idx, llr) in per.items():
+        code = codes[c]
+        rows = rng.choice(len(idx), 6, replace=False)
+        ref = oracle_mod.decode(code.row_ptr, code.col_idx, code.n, llr[rows].astype(np.float64), **kw)
+        for k, r in enumerate(rows):
+            f = idx[r]
+            xg = got["x"][offsets[f]:offsets[f + 1]]
+            if got["iters"][f] == ref["iters"][k]:
+                assert np.abs(xg - ref["x"][k]).max() <= 1e-4, (code.name, f)
+            else:
+                assert_stop_near_threshold(oracle_mod, code, llr[r], got["iters"][f], ref["iters"][k], mu=3.0,
+                                           rho=1.9, eps=1e-5)
