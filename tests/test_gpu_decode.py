@@ -197,6 +197,35 @@ def test_wide_codes_full_bench_size(gpu, oracle_mod, name, seed, tile):
     assert_parity(code, {k: v[sample] for k, v in got.items()}, ref, 1e-4, min_clean=0.25)
 
 
+@pytest.mark.parametrize("name,hseed", [("C1056", 0), ("C4000", 2)])
+def test_precision_full_bench_size(gpu, oracle_mod, name, hseed):
+    """`bench.py --workload precision` at full size: 10^5 frames at 2.5 and
+    4.0 dB (LLR seeds 200, 201), 300 fixed iterations, the library's default
+    tile, RESIDENT.  Eight of the bench's 48 sampled frames per point against
+    the oracle: FP32 state within 1e-4 and 16-bit fixed-point state within 5e-3
+    of the FP64 decode on every one of them."""
+    import torch
+
+    code = I.benchmark_code(name, hseed)
+    F = 100_000
+    C = gpu.Code(code)
+    try:
+        for pt, snr in enumerate((2.5, 4.0)):
+            llr = I.awgn_llr(code, snr, F, 200 + pt)
+            sample = np.linspace(0, F - 1, 48).astype(int)[::6]
+            ref = oracle_decode(oracle_mod, code, llr[sample], mu=MU, rho=RHO, eps=0.0, max_iter=300)
+            d_llr = torch.from_numpy(llr).cuda()
+            for state, tol in (("f32", 1e-4), ("q16", 5e-3)):
+                p = gpu.make_params(mu=MU, rho=RHO, eps=0.0, max_iter=300, state=state, schedule="resident")
+                x = gpu.decode(C, d_llr, p)["x"][torch.from_numpy(sample).cuda()].cpu().numpy()
+                err = np.abs(x - ref["x"]).max()
+                print(f"{name} {snr} dB {state}: max|x - x_oracle| = {err:.3e}")
+                assert err <= tol, (name, snr, state, err)
+            del d_llr
+    finally:
+        C.close()
+
+
 @pytest.mark.parametrize("snr,seed", [(2.5, 202), (1.5, 303)])
 def test_fp16_state(gpu, oracle_mod, c1056, snr, seed):
     """FP16 z/lambda storage (FP32 arithmetic): every frame within 5e-3 of the oracle."""

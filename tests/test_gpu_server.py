@@ -4,6 +4,7 @@ import time
 import numpy as np
 import pytest
 
+from _stopping import assert_stop_near_threshold
 from paper_1204_0556_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -165,3 +166,51 @@ def test_destroy_drains_submitted_frames(gpu, server_codes):
         srv.submit(cid, I.awgn_llr(codes[1], 2.0, 4, 600 + r), gpu.make_params(eps=1e-5, max_iter=200,
                                                                                 iters_per_launch=8))
     srv.close()  # returns after the worker finished every submitted frame
+
+
+def test_served_stream_of_the_bench(gpu, oracle_mod, server_codes):
+    """The served workload of `bench.py --workload served` in its configuration
+    (C96 / C1056 / C2640 / C8000 with the bench's seeds, codes drawn per request
+    by Philox key 6, the bench's pools of 2048 frames per code, eps = 1e-5, at
+    most 1000 iterations, rounds of 8 iterations, 8 GB budget), 20,000 one-frame
+    requests queued as fast as they can be submitted: every result equals
+    lpdec_decode of the same frame, and two frames per code match the oracle."""
+    import torch
+
+    codes, handles = server_codes
+    POOL, R = 2048, 20_000
+    snr_rng = np.random.Generator(np.random.Philox(key=7))
+    pools = [I.awgn_llr(c, snr_rng.uniform(1.5, 4.5, POOL), POOL, 8 + 10 * k) for k, c in enumerate(codes)]
+    which = np.random.Generator(np.random.Philox(key=6)).integers(0, 4, R).astype(np.int32)
+    cursor = [0, 0, 0, 0]
+    frame_of = np.zeros(R, dtype=np.int64)
+    for i, c in enumerate(which):
+        frame_of[i] = cursor[c]
+        cursor[c] = (cursor[c] + 1) % POOL
+    kw = dict(mu=3.0, rho=1.9, eps=1e-5, max_iter=1000)
+    p = gpu.make_params(state="f32", iters_per_launch=8, **kw)
+    srv = gpu.Server(budget_bytes=8 << 30)
+    try:
+        ids = [srv.add_code(h) for h in handles]
+        rids = [srv.submit(ids[c], pools[c][frame_of[i]], p) for i, c in enumerate(which)]
+        got = [srv.poll(rid, ids[c], 1, timeout_ms=300_000) for rid, c in zip(rids, which)]
+    finally:
+        srv.close()
+    pr = gpu.make_params(state="f32", schedule="resident", **kw)
+    for c in range(4):
+        ref = {k: v.cpu().numpy() for k, v in gpu.decode(handles[c], torch.from_numpy(pools[c]).cuda(), pr).items()}
+        for i in np.nonzero(which == c)[0]:
+            g, f = got[i], frame_of[i]
+            assert g is not None
+            assert np.array_equal(g["x"][0], ref["x"][f]), (codes[c].name, i)
+            assert np.array_equal(g["bits"][0], ref["bits"][f]), (codes[c].name, i)
+            assert g["iters"][0] == ref["iters"][f] and g["cert"][0] == ref["cert"][f], (codes[c].name, i)
+        rows = np.nonzero(which == c)[0][:2]
+        llr = np.stack([pools[c][frame_of[i]] for i in rows])
+        oref = oracle_mod.decode(codes[c].row_ptr, codes[c].col_idx, codes[c].n, llr.astype(np.float64), **kw)
+        for k, i in enumerate(rows):
+            if got[i]["iters"][0] == oref["iters"][k]:
+                assert np.abs(got[i]["x"][0] - oref["x"][k]).max() <= 1e-4, (codes[c].name, i)
+            else:
+                assert_stop_near_threshold(oracle_mod, codes[c], llr[k], got[i]["iters"][0], oref["iters"][k],
+                                           mu=3.0, rho=1.9, eps=1e-5)
