@@ -311,7 +311,10 @@ LPDEC_API int lpdec_decode_noalloc(const lpdec_code *code, int32_t n_frames, con
  * per frame, early exit by the stopping test).  Each code's rounds follow one
  * another on its own stream without waiting for the other codes' rounds.
  * Requests that arrive while a code's round is on the GPU join its next round.
- * A frame's result is identical to lpdec_decode of that frame alone.
+ * A frame's result is identical to lpdec_decode of that frame alone.  While
+ * rounds are in flight the scheduler thread polls their completion (it keeps
+ * one host core busy, yielding it between polls); it sleeps when no frame is
+ * queued or in flight.
  *   device_budget_bytes: upper bound on the device memory of all slot pools.
  *   cuda_stream: work already queued on this stream (NULL: the legacy default
  *                stream) completes before a code's first round; each code's
