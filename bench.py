@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--served-rate", type=float, default=2e5, help="offered load, frames/s")
     ap.add_argument("--served-requests", type=int, default=200_000)
     ap.add_argument("--served-round", type=int, default=8, help="ADMM iterations per server round")
+    ap.add_argument("--served-round-n8000", type=int, default=0,
+                    help="rounds of the n=8000 code, whose frames run longest (0: --served-round)")
     ap.add_argument("--mixed-frames", type=int, default=30_000)
     ap.add_argument("--precision-frames", type=int, default=100_000)
     return ap.parse_args()
@@ -488,7 +490,12 @@ def run_served(args):
     # is cycled through; a request's frame is drawn once per request.
     POOL = 2048
     pools = [I.awgn_llr(c, snr_rng.uniform(1.5, 4.5, POOL), POOL, 8 + 10 * k) for k, c in enumerate(codes)]
-    p = lpdec.make_params(mu=MU, rho=RHO, eps=1e-5, max_iter=1000, state="f32", iters_per_launch=args.served_round)
+    # A code's rounds length is its own parameter: the long C8000 frames may take
+    # longer rounds (less bookkeeping per iteration) without delaying the others.
+    rounds = [args.served_round] * 3 + [args.served_round_n8000 or args.served_round]
+    ps = [lpdec.make_params(mu=MU, rho=RHO, eps=1e-5, max_iter=1000, state="f32", iters_per_launch=r)
+          for r in rounds]
+    p = ps[0]
     tiles = autotune_codes(lpdec, handles, pools, "f32")
     srv = lpdec.Server(budget_bytes=8 << 30)
     ids = [srv.add_code(h) for h in handles]
@@ -510,7 +517,7 @@ def run_served(args):
     # one-time set-up of the server, hundreds of MB of device and pinned host
     # memory); one request per code is served before the timed stream.
     for c in range(4):
-        st = sub_fn(srv.handle, ids[c], 1, ptrs[c][POOL - 1], ctypes.byref(p), ctypes.byref(rid_c))
+        st = sub_fn(srv.handle, ids[c], 1, ptrs[c][POOL - 1], ctypes.byref(ps[c]), ctypes.byref(rid_c))
         if st == 0:
             st = poll_fn(srv.handle, int(rid_c.value), -1, outx[c].ctypes.data, outb[c].ctypes.data,
                          it_buf.ctypes.data, ce_buf.ctypes.data)
@@ -531,7 +538,9 @@ def run_served(args):
     arr = arrivals.tolist()
     rid_l = [0] * R
     lag_l = [0.0] * R
-    h, p_ref, rid_ref, pc = srv.handle, ctypes.byref(p), ctypes.byref(rid_c), time.perf_counter
+    h, rid_ref, pc = srv.handle, ctypes.byref(rid_c), time.perf_counter
+    p_refs = [ctypes.byref(q) for q in ps]
+    req_p = [p_refs[c] for c in req_code]
     x_ptr = [o.ctypes.data for o in outx]
     b_ptr = [o.ctypes.data for o in outb]
     it_ptr, ce_ptr = it_buf.ctypes.data, ce_buf.ctypes.data
@@ -553,11 +562,11 @@ def run_served(args):
         a = arr[i]
         while pc() - t0 < a:
             pass
-        st = sub_fn(h, req_id[i], 1, req_ptr[i], p_ref, rid_ref)
+        st = sub_fn(h, req_id[i], 1, req_ptr[i], req_p[i], rid_ref)
         while st == lpdec.LPDEC_EBUSY:  # back-pressure: the queue is full, wait for the server
             busy_waits[0] += 1
             time.sleep(0.0005)
-            st = sub_fn(h, req_id[i], 1, req_ptr[i], p_ref, rid_ref)
+            st = sub_fn(h, req_id[i], 1, req_ptr[i], req_p[i], rid_ref)
         if st != 0:
             raise RuntimeError(lpdec.lpdec_last_error())
         rid_l[i] = rid_c.value
@@ -605,7 +614,7 @@ def run_served(args):
         "gpu_busy_frac": ctr["round_gpu_ms"] / max(1e-9, wall * 1000.0),
         "config": {"codes": "C96, C1056, C2640, C8000 (irregular dc 6..20, dv 3), uniform per request",
                    "snr": "Eb/N0 uniform in [1.5, 4.5] dB", "eps": 1e-5, "max_iter": 1000,
-                   "iters_per_round": args.served_round, "budget_bytes": 8 << 30,
+                   "iters_per_round": {names[c]: rounds[c] for c in range(4)}, "budget_bytes": 8 << 30,
                    "arrivals": f"Poisson, {args.served_rate:.0f} frames/s, {R} one-frame requests",
                    "frames": "2048 seeded frames per code, cycled"},
         "mean_iters": {names[c]: float(iters[which == c].mean()) for c in range(4)},
