@@ -177,11 +177,11 @@ KERNEL_SOURCES = ("lpdec_device.cuh", "lpdec_kclass.cuh", "lpdec_internal.h")
 MEASURED_COUNTERS = {
     # C1056, 8000 frames x 300 iterations, tile 6 x 160 (instruction counters); traffic from the
     # bench's full-size launch (4 x 10^4 frames, tile 6 x 160)
-    "C1056/resident/f32": {"hash": "5be0f50773309bed", "fp32_ops": 53835, "warp_inst": 3957.4,
-                           "traffic": 174_423_296 + 165_346_048, "traffic_frames": 40000},
+    "C1056/resident/f32": {"hash": "8d57f3c0b45d2c40", "fp32_ops": 53835, "warp_inst": 3957.4,
+                           "traffic": 174_958_592 + 165_210_880, "traffic_frames": 40000},
     # 608 frames x 300 iterations; C8000 at tile 1 x 896, C4000 at 2 x 416 (no full-size traffic capture)
-    "C8000/resident/f32": {"hash": "5be0f50773309bed", "fp32_ops": 635319, "warp_inst": 72441.4},
-    "C4000/resident/f32": {"hash": "5be0f50773309bed", "fp32_ops": 255646, "warp_inst": 28131.1},
+    "C8000/resident/f32": {"hash": "8d57f3c0b45d2c40", "fp32_ops": 635319, "warp_inst": 72441.4},
+    "C4000/resident/f32": {"hash": "8d57f3c0b45d2c40", "fp32_ops": 255646, "warp_inst": 28131.1},
 }
 
 

@@ -945,7 +945,10 @@ __device__ __forceinline__ bool frame_run(const CodeView &c, const IterCfg &p, i
                 }
                 inv_dv = 1.0f / (float)DV;
                 const float x = __saturatef((acc - gi * p.mu_inv) * inv_dv);
-                sm.x[i] = x;
+                // x is read only by the check update of a residual iteration and
+                // by the outputs, which follow a residual iteration (the last
+                // one, or the one that stops); a folded iteration need not store it
+                if (!fold) sm.x[i] = x;
                 if (fold) {
                     const float rx = p.rho * x;
 #pragma unroll
